@@ -1,0 +1,341 @@
+"""Benchmark of the full triangle-centrality path on GB300.
+
+One step = one pass of the whole path over one synthetic graph already
+resident in HBM as a pair list: tc_build_csr (symmetrise, de-duplicate,
+degree order, orientation, plan) + tc_count (△(v), △(G), edge flags) +
+tc_centrality (exact numerators, one division) + tc_graph_free, all through
+the C ABI.  value = undirected edges processed per second over the timed
+steps (whole job; under torchrun every rank processes its own graph, seeded
+by rank: weak scaling, no collective on the data path).
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead (the reference arm; there is no reference implementation to run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "edges/s for full TC (build + count + centrality), exact"
+
+# Workloads: name -> generator spec
+WORKLOADS = {
+    "rmat-s24-ef16": dict(kind="rmat", scale=24, edge_factor=16, seed=0x5EED0018),
+    "rmat-s12-ef16": dict(kind="rmat", scale=12, edge_factor=16, seed=0x5EED0000),
+    "rmat-s20-ef16": dict(kind="rmat", scale=20, edge_factor=16, seed=0x5EED0014),
+    "grid4096-diag05-cl21": dict(kind="grid", side=4096, pdiag=0.05, gamma=2.1, mean_deg=4.0,
+                                 seed=0x5EED0002),
+}
+DEFAULT_WORKLOAD = "rmat-s24-ef16"
+
+
+def generate(spec: dict, rank: int = 0):
+    import graphgen as gg
+    seed = spec["seed"] + 0x1000 * rank
+    if spec["kind"] == "rmat":
+        return gg.rmat(spec["scale"], spec["edge_factor"], seed=seed)
+    return gg.grid_chung_lu(spec["side"], spec["pdiag"], spec["gamma"], spec["mean_deg"], seed=seed)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(",") for r in self.f.read().splitlines() if r.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+                for k, name in enumerate(names):
+                    if r[5 + k].strip().lower().startswith("active"):
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        # samples under load: the SM clock is read while kernels run; the
+        # median is over every sample taken inside the timed region
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ our path
+def run_ours(args, spec, wl_name):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2105_00110_gb300 as tcg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tcg.build()
+
+    src_np, dst_np, n = generate(spec, rank)
+    np_pairs = len(src_np)
+    d_src = torch.from_numpy(src_np).to(dev)
+    d_dst = torch.from_numpy(dst_np).to(dev)
+    h_src = torch.from_numpy(src_np).pin_memory()
+    h_dst = torch.from_numpy(dst_np).pin_memory()
+    del src_np, dst_np
+    stream = torch.cuda.current_stream(dev)
+
+    tri = torch.empty(n, dtype=torch.uint64, device=dev)
+    numer = torch.empty(n, dtype=torch.uint64, device=dev)
+    tcv = torch.empty(n, dtype=torch.float64, device=dev)
+    h_tc = torch.empty(n, dtype=torch.float64).pin_memory()
+    h_tri = torch.empty(n, dtype=torch.uint64).pin_memory()
+    flag_buf = [None]
+
+    def step(src, dst, to_host=False):
+        g = tcg.tc_build_csr(src, dst, n, stream)
+        m = tcg.tc_graph_info(g)[1]
+        if flag_buf[0] is None or flag_buf[0].numel() < m:
+            flag_buf[0] = torch.empty(max(m, 1), dtype=torch.uint8, device=dev)
+        st, total = tcg.tc_count(g, tri, flag_buf[0][:max(m, 1)] if m else None, stream)
+        tcg.tc_centrality(g, numer, tcv, stream)
+        if to_host:
+            h_tc.copy_(tcv, non_blocking=True)
+            h_tri.copy_(tri, non_blocking=True)
+        if not to_host and stats_box[0] is None:
+            stats_box[0] = tcg.tc_get_stats(g)
+        tcg.tc_graph_free(g)
+        return m, total
+
+    stats_box = [None]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---------------- device-resident timing
+    for _ in range(args.warmup):
+        m, total = step(d_src, d_dst)
+    stats = stats_box[0]
+    tcg.tc_profile_reset()
+    tcg.tc_profile_enable(True)
+    launches0 = tcg.tc_launch_count()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    edges = 0
+    for _ in range(args.steps):
+        m, total = step(d_src, d_dst)
+        edges += m
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    tcg.tc_profile_enable(False)
+    launches = tcg.tc_launch_count() - launches0
+    prof = tcg.tc_profile_read()
+    t_ms = ev0.elapsed_time(ev1)
+
+    # ---------------- end to end from pinned host buffers
+    for _ in range(max(1, args.warmup // 2)):
+        step(h_src, h_dst, to_host=True)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_edges = 0
+    for _ in range(args.steps):
+        m2, _ = step(h_src, h_dst, to_host=True)
+        e2e_edges += m2
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+
+    t_max, e2e_max = t_ms, e2e_ms
+    edges_all, e2e_edges_all = edges, e2e_edges
+    if world > 1:
+        agg = torch.tensor([t_ms, e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(agg, op=dist.ReduceOp.MAX)
+        cnt = torch.tensor([edges, e2e_edges], dtype=torch.float64, device=dev)
+        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
+        t_max, e2e_max = float(agg[0]), float(agg[1])
+        edges_all, e2e_edges_all = int(cnt[0]), int(cnt[1])
+
+    if rank == 0:
+        peak, peak_kind = peaks()
+        # the dominant kernel of the step and its algorithmic bytes per launch
+        kern = {k: v for k, v in prof.items()}
+        top = max(kern.items(), key=lambda kv: kv[1][1]) if kern else None
+        bytes_per = {"count_warp": stats["count_bytes_warp"], "count_cta": stats["count_bytes_cta"],
+                     "gather": stats["centrality_bytes"]}
+        roof = None
+        if top and top[0] in bytes_per:
+            name, (launch_n, tot_ms) = top
+            avg_s = tot_ms / launch_n / 1e3
+            achieved = bytes_per[name] / avg_s / 1e9
+            roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1),
+                    "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "algorithmic_bytes_per_launch": bytes_per[name],
+                    "avg_launch_ms": round(tot_ms / launch_n, 4)}
+        step_ms = t_max / args.steps
+        kernel_ms = {k: round(v[1] / args.steps, 4) for k, v in sorted(kern.items(), key=lambda kv: -kv[1][1])}
+        count_ms = sum(v for k, v in kernel_ms.items() if k.startswith("count"))
+        gather_ms = kernel_ms.get("gather", 0.0)
+        cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu) else None
+        line = {
+            "metric": METRIC,
+            "value": edges_all / (t_max / 1e3),
+            "unit": "edges/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": step_ms,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": wl_name, "n": n, "m": m, "pairs": np_pairs,
+                       "generator": spec, "triangles": total,
+                       "l2": "inputs larger than L2 (pair list %.1f GB per step)" % (np_pairs * 8 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "clocks": clocks,
+            "e2e": {"value": e2e_edges_all / (e2e_max / 1e3), "unit": "edges/s",
+                    "h2d_bytes_per_step": 2 * np_pairs * 4,
+                    "d2h_bytes_per_step": n * 8 * 2 + 8},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "phases_ms_per_step": kernel_ms,
+            "count_plus_centrality_edges_per_s": (m / ((count_ms + gather_ms) / 1e3)) if count_ms else None,
+            "graph_stats": stats,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- oracle side
+CPU_SAMPLE = dict(kind="rmat", scale=18, edge_factor=16, seed=0x5EED0012)
+
+
+def oracle_pass(spec):
+    """Full triangle centrality by the oracle; returns (edges, seconds)."""
+    import oracle
+    s, d, n = generate(spec)
+    t0 = time.perf_counter()
+    r = oracle.run(s, d, n, "fast")
+    dt = time.perf_counter() - t0
+    return len(r["adj"]) // 2, dt
+
+
+def cpu_baseline(args):
+    m, dt = oracle_pass(CPU_SAMPLE)
+    return {"value": m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": "R-MAT scale 18, edge factor 16, same (a,b,c,d), full TC by the oracle "
+                      "(canonical CSR, degree-ordered listing, Definition 1 numerators, exact "
+                      "division), single thread, %.1f s" % dt}
+
+
+def run_reference(args, wl_name):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    spec = dict(kind="rmat", scale=16, edge_factor=16, seed=0x5EED0010)
+    for _ in range(args.warmup):
+        oracle_pass(spec)
+    tot_m, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        m, dt = oracle_pass(spec)
+        tot_m += m
+        tot_t += dt
+    val = tot_m / tot_t
+    sample = ("each step: R-MAT scale 16, edge factor 16, same (a,b,c,d) as the workload, full "
+              "TC by the oracle, single thread (a bounded sample of %s)" % wl_name)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "edges/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": {"workload": wl_name},
+        "cpu_baseline": {"value": val, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        run_reference(args, args.workload)
+    else:
+        run_ours(args, WORKLOADS[args.workload], args.workload)
+
+
+if __name__ == "__main__":
+    main()

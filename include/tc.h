@@ -1,0 +1,203 @@
+/*
+ * tc.h — C ABI of the GB300 triangle-centrality library (libtc_gb300.so).
+ *
+ * Triangle centrality (P. Burkhardt, "Triangle Centrality", Definition 1):
+ *
+ *   TC(v) = ( ⅓ Σ_{u ∈ N△[v]} △(u) + Σ_{w ∈ N(v) \ N△(v)} △(w) ) / △(G)
+ *
+ * where △(v) is the number of triangles on v, △(G) the number in G,
+ * N△(v) = { u ∈ N(v) : N(u) ∩ N(v) ≠ ∅ } the triangle neighbours of v and
+ * N△[v] = {v} ∪ N△(v) (section "Notation").  The library computes it in
+ * the four steps of the paper's elementary algorithm (section "Algorithm",
+ * figure "Triangle centrality elementary algorithm"; Algorithm 2):
+ *
+ *   tc_build_csr   simple undirected graph from a pair list, degree order
+ *                  π (degree, then label) and orientation N_H / N_L
+ *                  (section "Notation"; Lemma 1's partition of N(v));
+ *   tc_count       △(v), △(G) and the in-a-triangle flag of every edge
+ *                  (steps 1 and 2; Procedure 1 and its alternative in
+ *                  the appendix "Alternative Triangle Neighbor Algorithm");
+ *   tc_centrality  the exact integer numerator
+ *                      numer(v) = Σ_{u∈N△[v]} △(u) + 3 Σ_{w∈N(v)\N△(v)} △(w)
+ *                                = 3 · △(G) · TC(v)
+ *                  and one binary64 division TC(v) = numer(v) / (3△(G)),
+ *                  rounded to nearest-even (step 3; Algorithm 2, whose
+ *                  (x/3 + y)/△(G) is the same quotient computed exactly).
+ *
+ * Conventions for every entry point:
+ *   - Vertex ids are 0-based in [0, n) (the paper labels 1..n).
+ *   - Pointers named d_* are device pointers, h_* host pointers.  Device
+ *     outputs are caller-allocated and caller-owned; the library never
+ *     frees them.  A tc_graph owns its own device memory until
+ *     tc_graph_free.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All
+ *     device work of a call is ordered on that stream.  A call that returns
+ *     a host scalar synchronises the stream before returning.
+ *   - No exception crosses the ABI.  On a negative status, outputs are
+ *     unspecified; *out pointers are set to NULL.
+ *   - One tc_graph must not be used by two calls at the same time; calls on
+ *     different graphs are independent.
+ *   - All integer results (counts, flags, numerators) are exact.
+ */
+#ifndef TC_GB300_H
+#define TC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* tc_stream;   /* the same type as cudaStream_t */
+typedef struct tc_graph tc_graph;        /* opaque */
+
+typedef enum {
+    TC_OK = 0,
+    TC_NO_TRIANGLES = 1,        /* warning: △(G) = 0; TC is NaN everywhere   */
+    TC_ERR_INVALID_ARG = -1,    /* bad pointer, size or vertex id             */
+    TC_ERR_OUT_OF_MEMORY = -2,  /* device or host allocation failed          */
+    TC_ERR_CUDA = -3,           /* any other CUDA runtime error               */
+    TC_ERR_OVERFLOW = -4,       /* 3·△(G) does not fit in 64 bits             */
+    TC_ERR_TIMEOUT = -5,        /* a bounded device-side wait gave up         */
+    TC_ERR_STATE = -6           /* call order violated (e.g. no tc_count yet) */
+} tc_status;
+
+/* tc_build_csr flags */
+#define TC_IN_DEVICE 1u   /* src/dst are device pointers (else pageable or pinned host) */
+#define TC_IDS_INT32 2u   /* src/dst hold int32_t ids (else int64_t)                     */
+
+/* Intersection strategies (tc_set_strategy).  AUTO lets the planner choose
+ * per work item by degree bucket; the others force one strategy for every
+ * item (used to test each strategy alone).                                   */
+#define TC_STRATEGY_AUTO    0
+#define TC_STRATEGY_BSEARCH 1   /* binary search of each streamed id in N_H(v) staged in shared memory */
+#define TC_STRATEGY_MERGE   2   /* warp-cooperative merge-path intersection of two sorted lists         */
+#define TC_STRATEGY_BITMAP  3   /* N_H(v) as a shared-memory bitmap over its id window (falls back to
+                                   BSEARCH for an item whose window does not fit)                       */
+
+/*
+ * Build the simple undirected graph G from `num_pairs` pairs (src[i],
+ * dst[i]) over vertices [0, n): pairs are symmetrised, self-loops and
+ * duplicates dropped (the set-up of the paper's section "Comparison").
+ * The graph is then relabelled by the degree order π of section "Notation"
+ * (ascending degree, ties by label) and every adjacency row sorted, so that
+ * the lower neighbours N_L(v) and the higher neighbours N_H(v) are the two
+ * contiguous halves of row v; this is the partition of Lemma 1.
+ *
+ *   src, dst   num_pairs ids each; device pointers if flags & TC_IN_DEVICE,
+ *              else host pointers (copied to the device inside the call);
+ *              int32_t if flags & TC_IDS_INT32, else int64_t.  Read only.
+ *   n          vertex count, 0 <= n <= 2^31 - 1.
+ *   out        receives the new graph (owned by the caller, release with
+ *              tc_graph_free), or NULL on error.
+ * Errors: TC_ERR_INVALID_ARG for NULL pointers with num_pairs > 0, negative
+ * sizes, n too large or any id outside [0, n); TC_ERR_OUT_OF_MEMORY;
+ * TC_ERR_CUDA.  Synchronises `stream`.
+ */
+tc_status tc_build_csr(const void* src, const void* dst, int64_t num_pairs, int64_t n,
+                       uint32_t flags, tc_stream stream, tc_graph** out);
+
+/*
+ * Steps 1-2 of the elementary algorithm: per-vertex triangle counts △(v),
+ * the total △(G) and the in-a-triangle flag of every edge (u ∈ N△(v)).
+ * Each triangle is found once, from the oriented edge joining its two
+ * lowest-ordered vertices, by intersecting their higher neighbourhoods
+ * (Procedure 1; appendix "Alternative Triangle Neighbor Algorithm").
+ *
+ *   d_tri        [n] uint64, caller labels: d_tri[v] = △(v).  May be NULL.
+ *   d_edge_flag  [m] uint8, aligned with the canonical edge list of
+ *                tc_graph_info: 1 if that edge lies in at least one
+ *                triangle, else 0.  May be NULL.
+ *   h_tri_total  receives △(G).  May be NULL.
+ * The counts and flags are also kept inside the graph for tc_centrality.
+ * Returns TC_OK, or TC_NO_TRIANGLES if △(G) = 0 (outputs still valid, all
+ * zero).  Synchronises `stream`.
+ */
+tc_status tc_count(tc_graph* g, uint64_t* d_tri, uint8_t* d_edge_flag,
+                   uint64_t* h_tri_total, tc_stream stream);
+
+/*
+ * Step 3: for every vertex the exact numerator
+ *   numer(v) = △(v) + Σ_{u ∈ N(v)} (u ∈ N△(v) ? 1 : 3) · △(u)
+ * (the core sum x plus three times the non-core sum y of Algorithm 2), and
+ * TC(v) = numer(v) / (3△(G)) rounded once to nearest-even binary64.  Uses
+ * the counts and flags of the most recent tc_count on g.
+ *
+ *   d_numer  [n] uint64, caller labels.  May be NULL.
+ *   d_tc     [n] double, caller labels.  May be NULL.  NaN everywhere if
+ *            △(G) = 0.
+ *   h_den    receives the denominator 3△(G).  May be NULL.
+ * Returns TC_OK, TC_NO_TRIANGLES, or TC_ERR_STATE if tc_count has not run
+ * on g.  Does not synchronise `stream`.
+ */
+tc_status tc_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, uint64_t* h_den,
+                        tc_stream stream);
+
+/*
+ * The division of step 3 on its own: d_tc[i] = d_numer[i] / den rounded to
+ * nearest-even binary64, exact for every 64-bit numerator and denominator
+ * (den = 0 gives NaN).  d_numer and d_tc are device arrays of n elements.
+ * Does not synchronise `stream`.
+ */
+tc_status tc_divide(const uint64_t* d_numer, int64_t n, uint64_t den, double* d_tc,
+                    tc_stream stream);
+
+/*
+ * The canonical edge list of g: m undirected edges (d_edge_u[i], d_edge_v[i])
+ * with d_edge_u[i] < d_edge_v[i], caller labels, sorted by (u, v).  The
+ * pointers stay owned by g and valid until tc_graph_free.  Any output
+ * pointer may be NULL.
+ */
+tc_status tc_graph_info(const tc_graph* g, int64_t* n, int64_t* m,
+                        const int32_t** d_edge_u, const int32_t** d_edge_v);
+
+/*
+ * Copies the canonical edge list into caller device buffers of m int32 each
+ * (d_u[i] < d_v[i], caller labels, sorted by (u, v)); either may be NULL.
+ * Ordered on `stream`; does not synchronise it.
+ */
+tc_status tc_copy_edges(const tc_graph* g, int32_t* d_u, int32_t* d_v, tc_stream stream);
+
+/* Shape statistics of g, computed at build time (host values). */
+typedef struct {
+    int64_t n, m;
+    int64_t max_degree;
+    int64_t max_out_degree;      /* max |N_H(v)|                                        */
+    double  sum_out_degree_sq;   /* Σ_v |N_H(v)|²                                       */
+    double  wedges;              /* Σ_v C(|N_H(v)|, 2): ids streamed by the count step   */
+    double  avg_degeneracy;      /* δ̄ = (1/m) Σ_{(v,u)∈E} min(d(v), d(u))              */
+    int64_t items_warp, items_cta;     /* work items of the count step per granularity */
+    double  count_bytes;         /* algorithmic DRAM bytes of the count step            */
+    double  count_bytes_warp;    /*   ... of its warp-item kernel                        */
+    double  count_bytes_cta;     /*   ... of its CTA-item kernel                         */
+    double  centrality_bytes;    /* algorithmic DRAM bytes of the gather + divide step  */
+} tc_graph_stats;
+
+tc_status tc_get_stats(const tc_graph* g, tc_graph_stats* out);
+
+/* Force one intersection strategy for later tc_count calls on g. */
+tc_status tc_set_strategy(tc_graph* g, int strategy);
+
+/*
+ * Optional device timing of every library kernel: when enabled, each
+ * launch is bracketed by CUDA events on its own stream, and
+ * tc_profile_read returns, per kernel name, the launch count and the
+ * summed event time since the last reset.  Timing adds two event records
+ * per launch; leave it off for throughput runs.
+ */
+tc_status tc_profile_enable(int on);
+tc_status tc_profile_reset(void);
+/* Fills up to `cap` entries; returns the number of distinct kernels in *count. */
+typedef struct { char name[48]; int64_t launches; double total_ms; } tc_kernel_time;
+tc_status tc_profile_read(tc_kernel_time* out, int cap, int* count);
+
+/* Number of kernels this library has launched since load (all threads). */
+int64_t tc_launch_count(void);
+
+void tc_graph_free(tc_graph* g);
+const char* tc_status_str(tc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TC_GB300_H */

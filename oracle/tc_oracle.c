@@ -56,42 +56,52 @@ typedef struct {
     int32_t* adj;     /* 2m, each row ascending */
 } og_graph;
 
-static int og_cmp_u64(const void* a, const void* b) {
-    uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+static int og_cmp_i32(const void* a, const void* b) {
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
     return (x > y) - (x < y);
 }
 
-/* Canonical simple undirected graph from arbitrary pairs.  Returns NULL if
- * an id is outside [0, n) or memory runs out. */
+/* Canonical simple undirected graph from arbitrary pairs: every pair (a, b)
+ * with a != b is entered as b in row a and a in row b (counting sort by
+ * row), each row is sorted and its repeats dropped.  Returns NULL if an id
+ * is outside [0, n) or memory runs out. */
 og_graph* og_build(const int32_t* src, const int32_t* dst, int64_t np, int64_t n) {
     if (n < 0 || np < 0 || n > INT32_MAX) return NULL;
-    uint64_t* key = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(2 * np + 1));
-    if (!key) return NULL;
-    int64_t k = 0;
-    for (int64_t i = 0; i < np; ++i) {
-        int64_t a = src[i], b = dst[i];
-        if (a < 0 || b < 0 || a >= n || b >= n) { free(key); return NULL; }
-        if (a == b) continue;                                  /* self-loop */
-        key[k++] = ((uint64_t)a << 32) | (uint64_t)b;          /* both directions */
-        key[k++] = ((uint64_t)b << 32) | (uint64_t)a;
-    }
-    qsort(key, (size_t)k, sizeof(uint64_t), og_cmp_u64);
-    int64_t u = 0;
-    for (int64_t i = 0; i < k; ++i)
-        if (i == 0 || key[i] != key[i - 1]) key[u++] = key[i];  /* duplicates */
+    for (int64_t i = 0; i < np; ++i)
+        if (src[i] < 0 || dst[i] < 0 || src[i] >= n || dst[i] >= n) return NULL;
+    int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!cnt) return NULL;
+    for (int64_t i = 0; i < np; ++i)
+        if (src[i] != dst[i]) { cnt[src[i] + 1] += 1; cnt[dst[i] + 1] += 1; }   /* self-loops dropped */
+    for (int64_t v = 0; v < n; ++v) cnt[v + 1] += cnt[v];
+    int64_t total = cnt[n];
+    int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * (size_t)(total + 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
     og_graph* g = (og_graph*)calloc(1, sizeof(og_graph));
-    if (!g) { free(key); return NULL; }
-    g->n = n;
-    g->m = u / 2;
-    g->ptr = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
-    g->adj = (int32_t*)malloc(sizeof(int32_t) * (size_t)(u + 1));
-    if (!g->ptr || !g->adj) { free(key); free(g->ptr); free(g->adj); free(g); return NULL; }
-    for (int64_t i = 0; i < u; ++i) {
-        g->ptr[(key[i] >> 32) + 1] += 1;
-        g->adj[i] = (int32_t)(key[i] & 0xFFFFFFFFu);
+    if (!buf || !fill || !g) { free(cnt); free(buf); free(fill); free(g); return NULL; }
+    memcpy(fill, cnt, sizeof(int64_t) * (size_t)(n + 1));
+    for (int64_t i = 0; i < np; ++i) {
+        if (src[i] == dst[i]) continue;
+        buf[fill[src[i]]++] = dst[i];          /* both directions */
+        buf[fill[dst[i]]++] = src[i];
     }
-    for (int64_t v = 0; v < n; ++v) g->ptr[v + 1] += g->ptr[v];
-    free(key);
+    free(fill);
+    g->n = n;
+    g->ptr = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!g->ptr) { free(cnt); free(buf); free(g); return NULL; }
+    int64_t out = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        int64_t b = cnt[v], e = cnt[v + 1];
+        qsort(buf + b, (size_t)(e - b), sizeof(int32_t), og_cmp_i32);
+        g->ptr[v] = out;
+        for (int64_t i = b; i < e; ++i)
+            if (i == b || buf[i] != buf[i - 1]) buf[out++] = buf[i];   /* duplicates dropped */
+    }
+    g->ptr[n] = out;
+    free(cnt);
+    g->m = out / 2;
+    g->adj = (int32_t*)realloc(buf, sizeof(int32_t) * (size_t)(out + 1));
+    if (!g->adj) g->adj = buf;
     return g;
 }
 

@@ -1,0 +1,293 @@
+"""Python binding of the GB300 triangle-centrality library (libtc_gb300.so).
+
+Argument marshalling only: every step of the path (graph construction,
+degree ordering, intersection, gather, division) runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  The binding has the
+C entry points under the same names (``tc_build_csr``, ``tc_count``,
+``tc_centrality``, ...) plus a small ``Graph`` convenience class.
+
+There is no CPU fallback: if the library has not been built, or no CUDA
+device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from .build import LIB, build  # noqa: F401
+
+TC_OK = 0
+TC_NO_TRIANGLES = 1
+TC_ERR_INVALID_ARG = -1
+TC_ERR_OUT_OF_MEMORY = -2
+TC_ERR_CUDA = -3
+TC_ERR_OVERFLOW = -4
+TC_ERR_TIMEOUT = -5
+TC_ERR_STATE = -6
+
+TC_IN_DEVICE = 1
+TC_IDS_INT32 = 2
+
+TC_STRATEGY_AUTO = 0
+TC_STRATEGY_BSEARCH = 1
+TC_STRATEGY_MERGE = 2
+TC_STRATEGY_BITMAP = 3
+STRATEGIES = {"auto": 0, "bsearch": 1, "merge": 2, "bitmap": 3}
+
+EXPORTED = ["tc_build_csr", "tc_count", "tc_centrality", "tc_divide", "tc_graph_info",
+            "tc_copy_edges", "tc_get_stats", "tc_set_strategy", "tc_profile_enable",
+            "tc_profile_reset", "tc_profile_read", "tc_launch_count", "tc_graph_free",
+            "tc_status_str"]
+
+
+class TCError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__("%s failed: %s (%d)" % (where, status_str(status), status))
+        self.status = status
+
+
+class GraphStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("max_degree", ctypes.c_int64), ("max_out_degree", ctypes.c_int64),
+                ("sum_out_degree_sq", ctypes.c_double), ("wedges", ctypes.c_double),
+                ("avg_degeneracy", ctypes.c_double),
+                ("items_warp", ctypes.c_int64), ("items_cta", ctypes.c_int64),
+                ("count_bytes", ctypes.c_double), ("count_bytes_warp", ctypes.c_double),
+                ("count_bytes_cta", ctypes.c_double), ("centrality_bytes", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError("libtc_gb300.so is not built: call paper_2105_00110_gb300.build()")
+        L = ctypes.CDLL(LIB)
+        vp, i64, u64, i32, u32 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64,
+                                  ctypes.c_int, ctypes.c_uint32)
+        L.tc_build_csr.restype = i32
+        L.tc_build_csr.argtypes = [vp, vp, i64, i64, u32, vp, ctypes.POINTER(vp)]
+        L.tc_count.restype = i32
+        L.tc_count.argtypes = [vp, vp, vp, ctypes.POINTER(u64), vp]
+        L.tc_centrality.restype = i32
+        L.tc_centrality.argtypes = [vp, vp, vp, ctypes.POINTER(u64), vp]
+        L.tc_divide.restype = i32
+        L.tc_divide.argtypes = [vp, i64, u64, vp, vp]
+        L.tc_graph_info.restype = i32
+        L.tc_graph_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                    ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.tc_copy_edges.restype = i32
+        L.tc_copy_edges.argtypes = [vp, vp, vp, vp]
+        L.tc_get_stats.restype = i32
+        L.tc_get_stats.argtypes = [vp, ctypes.POINTER(GraphStats)]
+        L.tc_set_strategy.restype = i32
+        L.tc_set_strategy.argtypes = [vp, i32]
+        L.tc_profile_enable.restype = i32
+        L.tc_profile_enable.argtypes = [i32]
+        L.tc_profile_reset.restype = i32
+        L.tc_profile_reset.argtypes = []
+        L.tc_profile_read.restype = i32
+        L.tc_profile_read.argtypes = [ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
+        L.tc_launch_count.restype = i64
+        L.tc_launch_count.argtypes = []
+        L.tc_graph_free.restype = None
+        L.tc_graph_free.argtypes = [vp]
+        L.tc_status_str.restype = ctypes.c_char_p
+        L.tc_status_str.argtypes = [i32]
+        _lib = L
+    return _lib
+
+
+def status_str(status: int) -> str:
+    try:
+        return lib().tc_status_str(int(status)).decode()
+    except Exception:  # library missing
+        return "status %d" % status
+
+
+def _check(status: int, where: str, ok=(TC_OK, TC_NO_TRIANGLES)) -> int:
+    if status not in ok:
+        raise TCError(status, where)
+    return status
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------- same names
+def tc_build_csr(src, dst, n: int, stream=None):
+    """Graph handle (ctypes.c_void_p) from pair arrays: CUDA or CPU torch
+    tensors, or numpy arrays, of int32 or int64."""
+    if isinstance(src, np.ndarray):
+        src = torch.from_numpy(np.ascontiguousarray(src))
+    if isinstance(dst, np.ndarray):
+        dst = torch.from_numpy(np.ascontiguousarray(dst))
+    if src.dtype != dst.dtype or src.shape != dst.shape or src.dim() != 1:
+        raise ValueError("src and dst must be 1-D with the same dtype and length")
+    if src.dtype not in (torch.int32, torch.int64):
+        raise ValueError("ids must be int32 or int64")
+    if src.is_cuda != dst.is_cuda:
+        raise ValueError("src and dst must be on the same device")
+    src = src.contiguous()
+    dst = dst.contiguous()
+    flags = (TC_IDS_INT32 if src.dtype == torch.int32 else 0) | (TC_IN_DEVICE if src.is_cuda else 0)
+    h = ctypes.c_void_p()
+    st = lib().tc_build_csr(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                            src.numel(), int(n), flags, _stream(stream), ctypes.byref(h))
+    _check(st, "tc_build_csr", ok=(TC_OK,))
+    return h
+
+
+def tc_count(g, tri=None, edge_flag=None, stream=None):
+    """(status, △(G)); fills tri [n] uint64 and edge_flag [m] uint8 if given."""
+    total = ctypes.c_uint64()
+    st = lib().tc_count(g, _dptr(tri), _dptr(edge_flag), ctypes.byref(total), _stream(stream))
+    _check(st, "tc_count")
+    return st, total.value
+
+
+def tc_centrality(g, numer=None, tc=None, stream=None):
+    """(status, 3△(G)); fills numer [n] uint64 and tc [n] float64 if given."""
+    den = ctypes.c_uint64()
+    st = lib().tc_centrality(g, _dptr(numer), _dptr(tc), ctypes.byref(den), _stream(stream))
+    _check(st, "tc_centrality")
+    return st, den.value
+
+
+def tc_divide(numer, den: int, out, stream=None):
+    st = lib().tc_divide(_dptr(numer), numer.numel(), int(den), _dptr(out), _stream(stream))
+    _check(st, "tc_divide", ok=(TC_OK,))
+
+
+def tc_graph_info(g):
+    n, m = ctypes.c_int64(), ctypes.c_int64()
+    pu, pv = ctypes.c_void_p(), ctypes.c_void_p()
+    _check(lib().tc_graph_info(g, ctypes.byref(n), ctypes.byref(m), ctypes.byref(pu),
+                               ctypes.byref(pv)), "tc_graph_info", ok=(TC_OK,))
+    return n.value, m.value, pu.value, pv.value
+
+
+def tc_copy_edges(g, u, v, stream=None):
+    _check(lib().tc_copy_edges(g, _dptr(u), _dptr(v), _stream(stream)), "tc_copy_edges", ok=(TC_OK,))
+
+
+def tc_get_stats(g) -> dict:
+    s = GraphStats()
+    _check(lib().tc_get_stats(g, ctypes.byref(s)), "tc_get_stats", ok=(TC_OK,))
+    return s.as_dict()
+
+
+def tc_set_strategy(g, strategy):
+    if isinstance(strategy, str):
+        strategy = STRATEGIES[strategy]
+    _check(lib().tc_set_strategy(g, int(strategy)), "tc_set_strategy", ok=(TC_OK,))
+
+
+def tc_profile_enable(on: bool = True):
+    lib().tc_profile_enable(1 if on else 0)
+
+
+def tc_profile_reset():
+    lib().tc_profile_reset()
+
+
+def tc_profile_read() -> dict:
+    cap = 64
+    arr = (KernelTime * cap)()
+    cnt = ctypes.c_int()
+    lib().tc_profile_read(arr, cap, ctypes.byref(cnt))
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(min(cnt.value, cap))}
+
+
+def tc_launch_count() -> int:
+    return int(lib().tc_launch_count())
+
+
+def tc_graph_free(g):
+    if g:
+        lib().tc_graph_free(g)
+
+
+# ------------------------------------------------------------ convenience
+class Graph:
+    """Owns a tc_graph; results come back as CUDA tensors in caller labels."""
+
+    def __init__(self, src, dst, n: int, stream=None):
+        self.h = tc_build_csr(src, dst, n, stream)
+        self.n, self.m, _, _ = tc_graph_info(self.h)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if self.h:
+            tc_graph_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def edges(self):
+        u = torch.empty(self.m, dtype=torch.int32, device=self.device)
+        v = torch.empty(self.m, dtype=torch.int32, device=self.device)
+        tc_copy_edges(self.h, u, v)
+        return u, v
+
+    def stats(self) -> dict:
+        return tc_get_stats(self.h)
+
+    def set_strategy(self, s):
+        tc_set_strategy(self.h, s)
+
+    def count(self, want_flags: bool = True, stream=None):
+        tri = torch.empty(self.n, dtype=torch.uint64, device=self.device)
+        flags = torch.empty(self.m, dtype=torch.uint8, device=self.device) if want_flags else None
+        st, total = tc_count(self.h, tri, flags, stream)
+        return tri, flags, total, st
+
+    def centrality(self, stream=None):
+        numer = torch.empty(self.n, dtype=torch.uint64, device=self.device)
+        tc = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        st, den = tc_centrality(self.h, numer, tc, stream)
+        return numer, tc, den, st
+
+
+def triangle_centrality(src, dst, n: int, strategy=None, stream=None) -> dict:
+    """One full pass: build, count, centrality.  Returns CUDA tensors."""
+    g = Graph(src, dst, n, stream)
+    try:
+        if strategy is not None:
+            g.set_strategy(strategy)
+        tri, flags, total, _ = g.count(stream=stream)
+        numer, tc, den, st = g.centrality(stream=stream)
+        eu, ev = g.edges()
+        return dict(n=g.n, m=g.m, tri=tri, flag=flags, total=total, numer=numer, tc=tc, den=den,
+                    status=st, edge_u=eu, edge_v=ev, stats=g.stats())
+    finally:
+        g.close()

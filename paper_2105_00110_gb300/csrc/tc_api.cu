@@ -1,0 +1,277 @@
+// C-ABI entry points, status strings, allocation and launch accounting.
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tc_internal.cuh"
+
+namespace tcx {
+
+tc_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return TC_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();  // clear the sticky-free allocation error
+        return TC_ERR_OUT_OF_MEMORY;
+    }
+    return TC_ERR_CUDA;
+}
+
+namespace {
+std::once_flag g_pool_once;
+std::atomic<long long> g_launches{0};
+
+struct timing_rec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<timing_rec> g_pending;      // launch-bracketing events not yet read
+std::vector<tc_kernel_time> g_totals;   // accumulated per name
+std::vector<cudaEvent_t> g_free_events;
+thread_local cudaEvent_t t_start = nullptr;
+
+cudaEvent_t take_event() {
+    if (!g_free_events.empty()) {
+        cudaEvent_t e = g_free_events.back();
+        g_free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void accumulate(const char* name, float ms) {
+    for (auto& t : g_totals)
+        if (std::strncmp(t.name, name, sizeof(t.name)) == 0) {
+            t.launches += 1;
+            t.total_ms += ms;
+            return;
+        }
+    tc_kernel_time k{};
+    std::strncpy(k.name, name, sizeof(k.name) - 1);
+    k.launches = 1;
+    k.total_ms = ms;
+    g_totals.push_back(k);
+}
+
+void drain_locked() {
+    for (auto& r : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess)
+            accumulate(r.name, ms);
+        g_free_events.push_back(r.a);
+        g_free_events.push_back(r.b);
+    }
+    g_pending.clear();
+}
+}  // namespace
+
+int sm_count() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached = v > 0 ? v : 1;
+    }
+    return cached;
+}
+
+tc_status dalloc(void** p, size_t bytes, cudaStream_t s) {
+    std::call_once(g_pool_once, [] {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            // keep freed blocks cached in this process so that repeated
+            // builds do not return memory to the driver in between
+            uint64_t threshold = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+        }
+    });
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return from_cuda(e);
+    }
+    return TC_OK;
+}
+
+void dfree(void* p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+void note_launch(const char* name, cudaStream_t s, int phase) {
+    if (phase == 0) {
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (g_prof_on) {
+            t_start = take_event();
+            cudaEventRecord(t_start, s);
+        } else {
+            t_start = nullptr;
+        }
+    } else {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        if (g_prof_on && t_start) {
+            cudaEvent_t b = take_event();
+            cudaEventRecord(b, s);
+            g_pending.push_back({name, t_start, b});
+            t_start = nullptr;
+        }
+    }
+}
+
+}  // namespace tcx
+
+using namespace tcx;
+
+extern "C" {
+
+const char* tc_status_str(tc_status s) {
+    switch (s) {
+        case TC_OK: return "ok";
+        case TC_NO_TRIANGLES: return "graph has no triangles (TC undefined, NaN)";
+        case TC_ERR_INVALID_ARG: return "invalid argument";
+        case TC_ERR_OUT_OF_MEMORY: return "out of memory";
+        case TC_ERR_CUDA: return "CUDA error";
+        case TC_ERR_OVERFLOW: return "3 * triangle count overflows 64 bits";
+        case TC_ERR_TIMEOUT: return "device wait timed out";
+        case TC_ERR_STATE: return "call order violated";
+    }
+    return "unknown status";
+}
+
+tc_status tc_build_csr(const void* src, const void* dst, int64_t num_pairs, int64_t n,
+                       uint32_t flags, tc_stream stream, tc_graph** out) {
+    if (!out) return TC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (num_pairs < 0 || n < 0 || n > INT32_MAX) return TC_ERR_INVALID_ARG;
+    if (num_pairs > 0 && (!src || !dst)) return TC_ERR_INVALID_ARG;
+    if (flags & ~(TC_IN_DEVICE | TC_IDS_INT32)) return TC_ERR_INVALID_ARG;
+    tc_graph* g = new (std::nothrow) tc_graph();
+    if (!g) return TC_ERR_OUT_OF_MEMORY;
+    cudaGetDevice(&g->device);
+    tc_status st;
+    try {
+        st = build_graph(g, src, dst, num_pairs, n, flags, (cudaStream_t)stream);
+    } catch (...) {
+        st = TC_ERR_CUDA;
+    }
+    if (st < 0) {
+        free_graph_memory(g);
+        cudaStreamSynchronize((cudaStream_t)stream);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return TC_OK;
+}
+
+tc_status tc_count(tc_graph* g, uint64_t* d_tri, uint8_t* d_edge_flag, uint64_t* h_tri_total,
+                   tc_stream stream) {
+    if (!g) return TC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->stream = s;
+    g->counted = 0;
+    TC_TRY(run_count(g, s));
+    if (d_tri) TC_TRY(export_tri(g, d_tri, s));
+    if (d_edge_flag) TC_TRY(export_flags(g, d_edge_flag, s));
+    unsigned long long total = 0;
+    TC_CUDA(cudaMemcpyAsync(&total, g->counters, 8, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    g->total = total;
+    g->counted = 1;
+    if (h_tri_total) *h_tri_total = total;
+    return total == 0 ? TC_NO_TRIANGLES : TC_OK;
+}
+
+tc_status tc_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, uint64_t* h_den,
+                        tc_stream stream) {
+    if (!g) return TC_ERR_INVALID_ARG;
+    if (!g->counted) return TC_ERR_STATE;
+    if (g->total > UINT64_MAX / 3) return TC_ERR_OVERFLOW;
+    g->stream = (cudaStream_t)stream;
+    TC_TRY(run_centrality(g, d_numer, d_tc, (cudaStream_t)stream));
+    if (h_den) *h_den = 3ull * g->total;
+    return g->total == 0 ? TC_NO_TRIANGLES : TC_OK;
+}
+
+tc_status tc_divide(const uint64_t* d_numer, int64_t n, uint64_t den, double* d_tc, tc_stream stream) {
+    if (n < 0 || (n > 0 && (!d_numer || !d_tc))) return TC_ERR_INVALID_ARG;
+    return run_divide(d_numer, n, den, d_tc, (cudaStream_t)stream);
+}
+
+tc_status tc_graph_info(const tc_graph* g, int64_t* n, int64_t* m, const int32_t** d_edge_u,
+                        const int32_t** d_edge_v) {
+    if (!g) return TC_ERR_INVALID_ARG;
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    if (d_edge_u) *d_edge_u = g->edge_u;
+    if (d_edge_v) *d_edge_v = g->edge_v;
+    return TC_OK;
+}
+
+tc_status tc_copy_edges(const tc_graph* g, int32_t* d_u, int32_t* d_v, tc_stream stream) {
+    if (!g) return TC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g->m > 0 && d_u) TC_CUDA(cudaMemcpyAsync(d_u, g->edge_u, g->m * 4, cudaMemcpyDeviceToDevice, s));
+    if (g->m > 0 && d_v) TC_CUDA(cudaMemcpyAsync(d_v, g->edge_v, g->m * 4, cudaMemcpyDeviceToDevice, s));
+    return TC_OK;
+}
+
+tc_status tc_get_stats(const tc_graph* g, tc_graph_stats* out) {
+    if (!g || !out) return TC_ERR_INVALID_ARG;
+    *out = g->stats;
+    return TC_OK;
+}
+
+tc_status tc_set_strategy(tc_graph* g, int strategy) {
+    if (!g || strategy < TC_STRATEGY_AUTO || strategy > TC_STRATEGY_BITMAP) return TC_ERR_INVALID_ARG;
+    g->strategy = strategy;
+    return TC_OK;
+}
+
+tc_status tc_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return TC_OK;
+}
+
+tc_status tc_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    drain_locked();
+    g_totals.clear();
+    return TC_OK;
+}
+
+tc_status tc_profile_read(tc_kernel_time* out, int cap, int* count) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    drain_locked();
+    int k = 0;
+    for (auto& t : g_totals) {
+        if (out && k < cap) out[k] = t;
+        ++k;
+    }
+    if (count) *count = k;
+    return TC_OK;
+}
+
+int64_t tc_launch_count(void) { return (int64_t)g_launches.load(); }
+
+void tc_graph_free(tc_graph* g) {
+    if (!g) return;
+    free_graph_memory(g);
+    cudaStreamSynchronize(g->stream);
+    delete g;
+}
+
+}  // extern "C"

@@ -1,0 +1,551 @@
+// tc_build_csr: simple undirected graph, degree order π, orientation and
+// the count-step plan, all on the device.
+//
+//  1. pairs -> canonical keys (min, max); self-loops become a sentinel
+//     (the set-up of section "Comparison": symmetrised, loop-free, simple)
+//  2. radix sort + unique -> the m undirected edges, caller labels
+//  3. degrees; π = sort by (degree, label) (section "Notation")
+//  4. both directions of every edge relabelled by π, radix sorted ->
+//     symmetric CSR in rank space, rows ascending, so each row is
+//     [N_L(v) | N_H(v)] (Lemma 1's partition, done by sorting)
+//  5. hstart (row split), edge_tail, twin and hrem of every head entry
+//  6. planner: per middle vertex v its work W(v) = Σ_{u∈N_L(v)} hrem, and
+//     the work items of the count step, heavy vertices split into chunks
+//
+// Radix sorts and scans use CUB (header-only, compiled into this library).
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "tc_internal.cuh"
+
+namespace tcx {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t n, int per_thread = 1) {
+    int64_t want = (n + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
+    int64_t cap = (int64_t)sm_count() * 16;
+    if (want < 1) want = 1;
+    return (int)std::min(want, cap);
+}
+
+#define GRID_STRIDE(i, n) \
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+template <typename T>
+__global__ void k_make_keys(const T* __restrict__ src, const T* __restrict__ dst, int64_t np,
+                            int64_t n, int bits, uint64_t* __restrict__ keys,
+                            unsigned int* __restrict__ err) {
+    GRID_STRIDE(i, np) {
+        int64_t a = (int64_t)src[i], b = (int64_t)dst[i];
+        uint64_t key = ~0ull;
+        if (a < 0 || b < 0 || a >= n || b >= n) {
+            atomicOr(err, 1u);
+        } else if (a != b) {
+            uint64_t lo = (uint64_t)(a < b ? a : b), hi = (uint64_t)(a < b ? b : a);
+            key = (lo << bits) | hi;
+        }
+        keys[i] = key;
+    }
+}
+
+__global__ void k_edges_degrees(const uint64_t* __restrict__ ukeys, int64_t m, int bits,
+                                int32_t* __restrict__ eu, int32_t* __restrict__ ev,
+                                int32_t* __restrict__ deg) {
+    const uint64_t mask = (1ull << bits) - 1;
+    GRID_STRIDE(e, m) {
+        uint64_t k = ukeys[e];
+        int32_t u = (int32_t)(k >> bits), v = (int32_t)(k & mask);
+        eu[e] = u;
+        ev[e] = v;
+        atomicAdd(&deg[u], 1);
+        atomicAdd(&deg[v], 1);
+    }
+}
+
+__global__ void k_rank_keys(const int32_t* __restrict__ deg, int64_t n, int bits,
+                            uint64_t* __restrict__ keys) {
+    GRID_STRIDE(v, n) keys[v] = ((uint64_t)deg[v] << bits) | (uint64_t)v;
+}
+
+__global__ void k_rank_apply(const uint64_t* __restrict__ sorted, int64_t n, int bits,
+                             int32_t* __restrict__ perm, int32_t* __restrict__ rank,
+                             int64_t* __restrict__ degr) {
+    const uint64_t mask = (1ull << bits) - 1;
+    GRID_STRIDE(r, n) {
+        uint64_t k = sorted[r];
+        int32_t v = (int32_t)(k & mask);
+        perm[r] = v;
+        rank[v] = (int32_t)r;
+        degr[r] = (int64_t)(k >> bits);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) degr[n] = 0;
+}
+
+__global__ void k_directed_keys(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                                const int32_t* __restrict__ rank, int64_t m, int bits,
+                                uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    GRID_STRIDE(e, m) {
+        uint64_t ru = (uint64_t)rank[eu[e]], rv = (uint64_t)rank[ev[e]];
+        keys[2 * e] = (ru << bits) | rv;
+        keys[2 * e + 1] = (rv << bits) | ru;
+        vals[2 * e] = (uint32_t)e;
+        vals[2 * e + 1] = (uint32_t)e;
+    }
+}
+
+// col, and the tail position of every canonical edge.
+__global__ void k_csr_cols(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                           int64_t e2, int bits, int32_t* __restrict__ col,
+                           int64_t* __restrict__ edge_tail) {
+    const uint64_t mask = (1ull << bits) - 1;
+    GRID_STRIDE(p, e2) {
+        uint64_t k = keys[p];
+        uint64_t row = k >> bits, c = k & mask;
+        col[p] = (int32_t)c;
+        if (c > row) edge_tail[vals[p]] = p;
+    }
+}
+
+// hstart[r]: first entry of row r with a label above r.
+__global__ void k_hstart(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                         int64_t n, int64_t* __restrict__ hstart) {
+    GRID_STRIDE(r, n) {
+        int64_t lo = row_ptr[r], hi = row_ptr[r + 1];
+        while (lo < hi) {
+            int64_t mid = lo + ((hi - lo) >> 1);
+            if ((int64_t)col[mid] <= r) lo = mid + 1; else hi = mid;
+        }
+        hstart[r] = lo;
+    }
+}
+
+// twin / hrem of head entries (col < row).
+__global__ void k_twin(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                       const int64_t* __restrict__ edge_tail, const int64_t* __restrict__ row_ptr,
+                       int64_t e2, int bits, int64_t* __restrict__ twin,
+                       int32_t* __restrict__ hrem) {
+    const uint64_t mask = (1ull << bits) - 1;
+    GRID_STRIDE(p, e2) {
+        uint64_t k = keys[p];
+        uint64_t row = k >> bits, c = k & mask;
+        if (c < row) {
+            int64_t t = edge_tail[vals[p]];
+            twin[p] = t;
+            hrem[p] = (int32_t)(row_ptr[c + 1] - t - 1);
+        } else {
+            twin[p] = -1;
+            hrem[p] = 0;
+        }
+    }
+}
+
+// ----------------------------------------------------------------- planner
+struct plan_params {
+    int64_t warp_cap;      // max |N_H(v)| of a warp item
+    int64_t cta_min_work;  // W(v) at or above which v becomes CTA items
+    int64_t cta_chunk;     // target work of one CTA item
+};
+
+struct plan_stats {
+    unsigned long long sum_h2, wedges, sum_dh, max_h, max_d;
+    unsigned long long cta_wedges, cta_head, cta_staged, cta_vertices;
+};
+
+// One warp per row: W(v), item counts (written in reverse rank order so
+// that the heaviest vertices come first), shape statistics.
+__global__ void k_plan_rows(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
+                            const int32_t* __restrict__ hrem, int64_t n, plan_params pp,
+                            int64_t* __restrict__ nw, int64_t* __restrict__ nc,
+                            int64_t* __restrict__ work, plan_stats* __restrict__ st) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long l_h2 = 0, l_w = 0, l_dh = 0, l_maxh = 0, l_maxd = 0;
+    unsigned long long c_w = 0, c_head = 0, c_staged = 0, c_v = 0;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+        int64_t b = row_ptr[r], h = hstart[r], e = row_ptr[r + 1];
+        unsigned long long w = 0;
+        for (int64_t p = b + lane; p < h; p += 32) w += (unsigned long long)hrem[p];
+        for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (lane == 0) {
+            int64_t hv = e - h, lv = h - b;
+            int64_t cw = 0, cc = 0;
+            if (w > 0 && hv > 0) {
+                if (hv > pp.warp_cap || (int64_t)w >= pp.cta_min_work) {
+                    cc = ((int64_t)w + pp.cta_chunk - 1) / pp.cta_chunk;
+                    if (cc > lv) cc = lv;
+                    if (cc < 1) cc = 1;
+                } else {
+                    cw = 1;
+                }
+            }
+            if (cc) {
+                c_w += w;
+                c_head += (unsigned long long)lv;
+                c_staged += (unsigned long long)hv;
+                c_v += 1;
+            }
+            nw[n - 1 - r] = cw;
+            nc[n - 1 - r] = cc;
+            work[r] = (int64_t)w;
+            l_h2 += (unsigned long long)(hv * hv);
+            l_w += w;
+            l_dh += (unsigned long long)((e - b) * hv);
+            l_maxh = l_maxh > (unsigned long long)hv ? l_maxh : (unsigned long long)hv;
+            l_maxd = l_maxd > (unsigned long long)(e - b) ? l_maxd : (unsigned long long)(e - b);
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&st->sum_h2, l_h2);
+        atomicAdd(&st->wedges, l_w);
+        atomicAdd(&st->sum_dh, l_dh);
+        atomicMax(&st->max_h, l_maxh);
+        atomicMax(&st->max_d, l_maxd);
+        atomicAdd(&st->cta_wedges, c_w);
+        atomicAdd(&st->cta_head, c_head);
+        atomicAdd(&st->cta_staged, c_staged);
+        atomicAdd(&st->cta_vertices, c_v);
+    }
+}
+
+__global__ void k_plan_emit(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
+                            int64_t n, const int64_t* __restrict__ nw, const int64_t* __restrict__ nc,
+                            const int64_t* __restrict__ ow, const int64_t* __restrict__ oc,
+                            int32_t* __restrict__ w_v, int64_t* __restrict__ w_pb,
+                            int64_t* __restrict__ w_pe, int32_t* __restrict__ c_v,
+                            int64_t* __restrict__ c_pb, int64_t* __restrict__ c_pe) {
+    GRID_STRIDE(i, n) {
+        int64_t r = n - 1 - i;
+        int64_t b = row_ptr[r], h = hstart[r];
+        if (nw[i]) {
+            int64_t o = ow[i];
+            w_v[o] = (int32_t)r;
+            w_pb[o] = b;
+            w_pe[o] = h;
+        }
+        int64_t k = nc[i];
+        if (k) {
+            int64_t o = oc[i], lv = h - b;
+            for (int64_t c = 0; c < k; ++c) {
+                c_v[o + c] = (int32_t)r;
+                c_pb[o + c] = b + lv * c / k;
+                c_pe[o + c] = b + lv * (c + 1) / k;
+            }
+        }
+    }
+}
+
+int bits_for(int64_t n) {
+    int b = 1;
+    while (b < 62 && ((int64_t)1 << b) < n) ++b;
+    return b;
+}
+
+// Owns every temporary of a build so that an early return releases them.
+struct scratch {
+    cudaStream_t s;
+    void* p[16] = {};
+    int k = 0;
+    explicit scratch(cudaStream_t st) : s(st) {}
+    template <typename T>
+    tc_status get(T** out, size_t count) {
+        void* q = nullptr;
+        TC_TRY(dalloc(&q, count * sizeof(T) + 16, s));
+        p[k++] = q;
+        *out = (T*)q;
+        return TC_OK;
+    }
+    ~scratch() { for (int i = 0; i < k; ++i) dfree(p[i], s); }
+};
+
+template <typename T>
+tc_status sort_keys(scratch& sc, cub::DoubleBuffer<T>& buf, int64_t count, int end_bit, cudaStream_t s) {
+    size_t bytes = 0;
+    TC_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, bytes, buf, count, 0, end_bit, s));
+    uint8_t* tmp = nullptr;
+    TC_TRY(sc.get(&tmp, bytes));
+    TC_CUDA(cub::DeviceRadixSort::SortKeys(tmp, bytes, buf, count, 0, end_bit, s));
+    return TC_OK;
+}
+
+}  // namespace
+
+void free_graph_memory(tc_graph* g) {
+    cudaStream_t s = g->stream;
+    void* ptrs[] = {g->edge_u, g->edge_v, g->perm, g->row_ptr, g->col, g->hstart, g->twin,
+                    g->hrem, g->edge_tail, g->plan.w_v, g->plan.w_pb, g->plan.w_pe,
+                    g->plan.c_v, g->plan.c_pb, g->plan.c_pe, g->tri, g->flag, g->numer,
+                    g->counters};
+    for (void* q : ptrs) dfree(q, s);
+}
+
+tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np, int64_t n,
+                      uint32_t flags, cudaStream_t s) {
+    g->n = n;
+    g->bits = bits_for(n);
+    g->stream = s;
+    const int bits = g->bits;
+    const bool i32 = (flags & TC_IDS_INT32) != 0;
+    const size_t id_bytes = i32 ? 4 : 8;
+    scratch sc(s);
+
+    // ---- 0. inputs on the device
+    const void* dsrc = src;
+    const void* ddst = dst;
+    if (!(flags & TC_IN_DEVICE) && np > 0) {
+        void *a = nullptr, *b = nullptr;
+        TC_TRY(sc.get((uint8_t**)&a, np * id_bytes));
+        TC_TRY(sc.get((uint8_t**)&b, np * id_bytes));
+        TC_CUDA(cudaMemcpyAsync(a, src, np * id_bytes, cudaMemcpyHostToDevice, s));
+        TC_CUDA(cudaMemcpyAsync(b, dst, np * id_bytes, cudaMemcpyHostToDevice, s));
+        dsrc = a;
+        ddst = b;
+    }
+
+    // ---- 1-2. canonical undirected edges
+    unsigned int* err = nullptr;
+    TC_TRY(sc.get(&err, 4));
+    TC_CUDA(cudaMemsetAsync(err, 0, 4, s));
+    uint64_t *ka = nullptr, *kb = nullptr;
+    int64_t m = 0;
+    int64_t* d_nsel = nullptr;
+    TC_TRY(sc.get(&d_nsel, 2));
+    if (np > 0) {
+        TC_TRY(sc.get(&ka, np));
+        TC_TRY(sc.get(&kb, np));
+        {
+            launch_scope ls("build_make_keys", s);
+            if (i32)
+                k_make_keys<int32_t><<<grid_for(np), kThreads, 0, s>>>(
+                    (const int32_t*)dsrc, (const int32_t*)ddst, np, n, bits, ka, err);
+            else
+                k_make_keys<int64_t><<<grid_for(np), kThreads, 0, s>>>(
+                    (const int64_t*)dsrc, (const int64_t*)ddst, np, n, bits, ka, err);
+            TC_LAUNCH_CHECK();
+        }
+        cub::DoubleBuffer<uint64_t> kbuf(ka, kb);
+        {
+            launch_scope ls("build_sort_pairs", s);
+            TC_TRY(sort_keys(sc, kbuf, np, 2 * bits, s));
+        }
+        uint64_t* sorted = kbuf.Current();
+        uint64_t* uniq = kbuf.Alternate();
+        size_t bytes = 0;
+        TC_CUDA(cub::DeviceSelect::Unique(nullptr, bytes, sorted, uniq, d_nsel, np, s));
+        uint8_t* tmp = nullptr;
+        TC_TRY(sc.get(&tmp, bytes));
+        {
+            launch_scope ls("build_unique", s);
+            TC_CUDA(cub::DeviceSelect::Unique(tmp, bytes, sorted, uniq, d_nsel, np, s));
+        }
+        int64_t h_sel = 0;
+        uint64_t last = 0;
+        unsigned int h_err = 0;
+        TC_CUDA(cudaMemcpyAsync(&h_sel, d_nsel, 8, cudaMemcpyDeviceToHost, s));
+        TC_CUDA(cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, s));
+        TC_CUDA(cudaStreamSynchronize(s));
+        if (h_err) return TC_ERR_INVALID_ARG;
+        if (h_sel > 0) {
+            TC_CUDA(cudaMemcpyAsync(&last, uniq + h_sel - 1, 8, cudaMemcpyDeviceToHost, s));
+            TC_CUDA(cudaStreamSynchronize(s));
+        }
+        m = h_sel - ((h_sel > 0 && last == ~0ull) ? 1 : 0);
+        ka = uniq;  // the m unique keys
+    }
+    if (m >= ((int64_t)1 << 32)) return TC_ERR_INVALID_ARG;  // edge ids are 32-bit
+    g->m = m;
+    const int64_t e2 = 2 * m;
+
+    // ---- graph-owned arrays
+    TC_TRY(dalloc((void**)&g->edge_u, (m + 1) * 4, s));
+    TC_TRY(dalloc((void**)&g->edge_v, (m + 1) * 4, s));
+    TC_TRY(dalloc((void**)&g->perm, (n + 1) * 4, s));
+    TC_TRY(dalloc((void**)&g->row_ptr, (n + 2) * 8, s));
+    TC_TRY(dalloc((void**)&g->col, (e2 + 1) * 4, s));
+    TC_TRY(dalloc((void**)&g->hstart, (n + 1) * 8, s));
+    TC_TRY(dalloc((void**)&g->twin, (e2 + 1) * 8, s));
+    TC_TRY(dalloc((void**)&g->hrem, (e2 + 1) * 4, s));
+    TC_TRY(dalloc((void**)&g->edge_tail, (m + 1) * 8, s));
+    TC_TRY(dalloc((void**)&g->tri, (n + 1) * 8, s));
+    TC_TRY(dalloc((void**)&g->numer, (n + 1) * 8, s));
+    TC_TRY(dalloc((void**)&g->flag, e2 + 16, s));
+    TC_TRY(dalloc((void**)&g->counters, 8 * 8, s));
+
+    // ---- 3. degrees and the order π
+    int32_t* deg = nullptr;
+    TC_TRY(sc.get(&deg, n + 1));
+    TC_CUDA(cudaMemsetAsync(deg, 0, (n + 1) * 4, s));
+    if (m > 0) {
+        launch_scope ls("build_edges_degrees", s);
+        k_edges_degrees<<<grid_for(m), kThreads, 0, s>>>(ka, m, bits, g->edge_u, g->edge_v, deg);
+        TC_LAUNCH_CHECK();
+    }
+    int32_t* rank = nullptr;
+    int64_t* degr = nullptr;
+    TC_TRY(sc.get(&rank, n + 1));
+    TC_TRY(sc.get(&degr, n + 2));
+    if (n > 0) {
+        uint64_t *ra = nullptr, *rb = nullptr;
+        TC_TRY(sc.get(&ra, n));
+        TC_TRY(sc.get(&rb, n));
+        {
+            launch_scope ls("build_rank_keys", s);
+            k_rank_keys<<<grid_for(n), kThreads, 0, s>>>(deg, n, bits, ra);
+            TC_LAUNCH_CHECK();
+        }
+        cub::DoubleBuffer<uint64_t> rbuf(ra, rb);
+        {
+            launch_scope ls("build_sort_rank", s);
+            TC_TRY(sort_keys(sc, rbuf, n, 2 * bits, s));
+        }
+        launch_scope ls("build_rank_apply", s);
+        k_rank_apply<<<grid_for(n), kThreads, 0, s>>>(rbuf.Current(), n, bits, g->perm, rank, degr);
+        TC_LAUNCH_CHECK();
+    } else {
+        TC_CUDA(cudaMemsetAsync(degr, 0, 8, s));
+    }
+    {
+        size_t bytes = 0;
+        TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, degr, g->row_ptr, n + 1, s));
+        uint8_t* tmp = nullptr;
+        TC_TRY(sc.get(&tmp, bytes));
+        launch_scope ls("build_row_ptr", s);
+        TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, bytes, degr, g->row_ptr, n + 1, s));
+    }
+
+    // ---- 4. rank-space symmetric CSR
+    uint64_t* dkeys = nullptr;
+    uint32_t* dvals = nullptr;
+    if (m > 0) {
+        uint64_t *da = nullptr, *db = nullptr;
+        uint32_t *va = nullptr, *vb = nullptr;
+        TC_TRY(sc.get(&da, e2));
+        TC_TRY(sc.get(&db, e2));
+        TC_TRY(sc.get(&va, e2));
+        TC_TRY(sc.get(&vb, e2));
+        {
+            launch_scope ls("build_directed_keys", s);
+            k_directed_keys<<<grid_for(m), kThreads, 0, s>>>(g->edge_u, g->edge_v, rank, m, bits, da, va);
+            TC_LAUNCH_CHECK();
+        }
+        cub::DoubleBuffer<uint64_t> kb2(da, db);
+        cub::DoubleBuffer<uint32_t> vb2(va, vb);
+        size_t bytes = 0;
+        TC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb2, vb2, e2, 0, 2 * bits, s));
+        uint8_t* tmp = nullptr;
+        TC_TRY(sc.get(&tmp, bytes));
+        {
+            launch_scope ls("build_sort_directed", s);
+            TC_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb2, vb2, e2, 0, 2 * bits, s));
+        }
+        dkeys = kb2.Current();
+        dvals = vb2.Current();
+        {
+            launch_scope ls("build_csr_cols", s);
+            k_csr_cols<<<grid_for(e2), kThreads, 0, s>>>(dkeys, dvals, e2, bits, g->col, g->edge_tail);
+            TC_LAUNCH_CHECK();
+        }
+    }
+    if (n > 0) {
+        launch_scope ls("build_hstart", s);
+        k_hstart<<<grid_for(n), kThreads, 0, s>>>(g->row_ptr, g->col, n, g->hstart);
+        TC_LAUNCH_CHECK();
+    }
+    if (m > 0) {
+        launch_scope ls("build_twin", s);
+        k_twin<<<grid_for(e2), kThreads, 0, s>>>(dkeys, dvals, g->edge_tail, g->row_ptr, e2, bits,
+                                                 g->twin, g->hrem);
+        TC_LAUNCH_CHECK();
+    }
+
+    // ---- 6. planner
+    plan_params pp{TC_WARP_CAP, 32768, 65536};
+    int64_t *nw = nullptr, *nc = nullptr, *ow = nullptr, *oc = nullptr, *work = nullptr;
+    plan_stats* dst_stats = nullptr;
+    TC_TRY(sc.get(&nw, n + 1));
+    TC_TRY(sc.get(&nc, n + 1));
+    TC_TRY(sc.get(&ow, n + 1));
+    TC_TRY(sc.get(&oc, n + 1));
+    TC_TRY(sc.get(&work, n + 1));
+    TC_TRY(sc.get(&dst_stats, 1));
+    TC_CUDA(cudaMemsetAsync(dst_stats, 0, sizeof(plan_stats), s));
+    TC_CUDA(cudaMemsetAsync(nw, 0, (n + 1) * 8, s));
+    TC_CUDA(cudaMemsetAsync(nc, 0, (n + 1) * 8, s));
+    if (n > 0) {
+        launch_scope ls("plan_rows", s);
+        int64_t warps = (n + 0);
+        int blocks = (int)std::min<int64_t>((warps * 32 + kThreads - 1) / kThreads,
+                                            (int64_t)sm_count() * 16);
+        k_plan_rows<<<std::max(blocks, 1), kThreads, 0, s>>>(g->row_ptr, g->hstart, g->hrem, n, pp,
+                                                             nw, nc, work, dst_stats);
+        TC_LAUNCH_CHECK();
+    }
+    {
+        size_t bytes = 0;
+        TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, nw, ow, n + 1, s));
+        uint8_t* tmp = nullptr;
+        TC_TRY(sc.get(&tmp, bytes));
+        launch_scope ls("plan_scan", s);
+        TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, bytes, nw, ow, n + 1, s));
+        TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, bytes, nc, oc, n + 1, s));
+    }
+    int64_t counts[2] = {0, 0};
+    plan_stats hst{};
+    TC_CUDA(cudaMemcpyAsync(&counts[0], ow + n, 8, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaMemcpyAsync(&counts[1], oc + n, 8, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaMemcpyAsync(&hst, dst_stats, sizeof(plan_stats), cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    g->plan.n_warp = counts[0];
+    g->plan.n_cta = counts[1];
+    TC_TRY(dalloc((void**)&g->plan.w_v, (counts[0] + 1) * 4, s));
+    TC_TRY(dalloc((void**)&g->plan.w_pb, (counts[0] + 1) * 8, s));
+    TC_TRY(dalloc((void**)&g->plan.w_pe, (counts[0] + 1) * 8, s));
+    TC_TRY(dalloc((void**)&g->plan.c_v, (counts[1] + 1) * 4, s));
+    TC_TRY(dalloc((void**)&g->plan.c_pb, (counts[1] + 1) * 8, s));
+    TC_TRY(dalloc((void**)&g->plan.c_pe, (counts[1] + 1) * 8, s));
+    if (n > 0 && counts[0] + counts[1] > 0) {
+        launch_scope ls("plan_emit", s);
+        k_plan_emit<<<grid_for(n), kThreads, 0, s>>>(g->row_ptr, g->hstart, n, nw, nc, ow, oc,
+                                                     g->plan.w_v, g->plan.w_pb, g->plan.w_pe,
+                                                     g->plan.c_v, g->plan.c_pb, g->plan.c_pe);
+        TC_LAUNCH_CHECK();
+    }
+
+    // ---- statistics (host)
+    tc_graph_stats& S = g->stats;
+    S.n = n;
+    S.m = m;
+    S.max_degree = (int64_t)hst.max_d;
+    S.max_out_degree = (int64_t)hst.max_h;
+    S.sum_out_degree_sq = (double)hst.sum_h2;
+    S.wedges = (double)hst.wedges;
+    S.avg_degeneracy = m ? (double)hst.sum_dh / (double)m : 0.0;
+    S.items_warp = counts[0];
+    S.items_cta = counts[1];
+    // Count step: stage N_H(v) once per middle vertex (4m), read each head
+    // entry's label, twin and hrem (16m), stream every wedge id (4 W), write
+    // the vertex counts (8n) and one flag byte per tail entry (m).
+    S.count_bytes = 4.0 * m + 16.0 * m + 4.0 * S.wedges + 8.0 * n + 1.0 * m;
+    {
+        // split by kernel: the CTA-item kernel stages N_H(v) of the heavy
+        // vertices, reads their head entries and streams their wedges; the
+        // warp-item kernel does the rest, including the count and flag writes
+        double cw = (double)hst.cta_wedges, ch = (double)hst.cta_head, chv = (double)hst.cta_staged;
+        S.count_bytes_cta = 4.0 * chv + 16.0 * ch + 4.0 * cw;
+        S.count_bytes_warp = S.count_bytes - S.count_bytes_cta;
+    }
+    // Gather: per vertex row_ptr, hstart, perm, △(v), numerator and TC out
+    // (8+8+4+8+8+8); per adjacency entry its label and the neighbour's count
+    // (4+8); per head entry twin and the mirrored flag (8+1); per tail entry
+    // its flag (1).
+    S.centrality_bytes = 44.0 * n + 12.0 * (double)e2 + 9.0 * m + 1.0 * m;
+    TC_CUDA(cudaStreamSynchronize(s));
+    return TC_OK;
+}
+
+}  // namespace tcx

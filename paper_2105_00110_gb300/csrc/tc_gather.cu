@@ -1,0 +1,163 @@
+// tc_centrality: the per-vertex gather and the one division of step 3 of
+// the elementary algorithm (section "Algorithm"; Algorithm 2).
+//
+// Algorithm 2 forms x = Σ_{u∈N△[v]} △(u) (core sum, v included),
+// s = Σ_{u∈N(v)} △(u) and y = s − x + △(v), then (x/3 + y)/△(G).  Here the
+// same quantity is kept exact as one integer
+//     numer(v) = x + 3y = △(v) + Σ_{u∈N(v)} (u ∈ N△(v) ? 1 : 3) · △(u)
+// and divided once by 3△(G).  u ∈ N△(v) is the edge flag of (v, u): for a
+// tail entry of row v (u above v) the flag sits at the entry itself, for a
+// head entry (u below v) at its twin, the canonical entry in row u.
+#include "tc_internal.cuh"
+
+namespace tcx {
+
+namespace {
+
+typedef unsigned long long ull;
+
+// a / b correctly rounded (nearest, ties to even).  Operands below 2^53 are
+// exact doubles, so one IEEE division is the answer.  Otherwise the
+// quotient is developed in base-2^64 digits (integer part, then two
+// fraction digits by 128-by-64-bit division), which always holds at least
+// 54 significant bits because a/b >= 2^-64 when a >= 1; the bits below
+// them and the last remainder form the sticky bit.
+__device__ double div_rn(ull a, ull b) {
+    if (b == 0) return __longlong_as_double(0x7ff8000000000000ll);
+    if (a == 0) return 0.0;
+    const ull lim = 1ull << 53;
+    if (a < lim && b < lim) return __ddiv_rn((double)a, (double)b);
+    ull q = a / b, r = a % b;
+    unsigned __int128 t = (unsigned __int128)r << 64;
+    ull f1 = (ull)(t / b);
+    r = (ull)(t % b);
+    t = (unsigned __int128)r << 64;
+    ull f2 = (ull)(t / b);
+    r = (ull)(t % b);
+    bool sticky = r != 0;
+    unsigned __int128 win;
+    int k, lead;   // lead: position of the leading one counted from the fraction's start
+    if (q) {
+        k = 63 - __clzll((long long)q);
+        win = ((unsigned __int128)q << 64) | f1;   // digits q.f1
+        lead = 64 + k;
+        sticky |= f2 != 0;
+    } else {
+        k = 63 - __clzll((long long)f1);
+        win = ((unsigned __int128)f1 << 64) | f2;  // digits 0.f1 f2
+        lead = 64 + k;
+    }
+    const int shift = lead - 53;                  // keep 54 bits: 53 + rounding bit
+    ull m54 = (ull)(win >> shift);
+    sticky |= (win & (((unsigned __int128)1 << shift) - 1)) != 0;
+    // value of the lowest kept bit: q-case 2^(k-53); f-case 2^(k-53-64)
+    int e = q ? (k - 53) : (k - 53 - 64);
+    ull rb = m54 & 1;
+    ull mant = m54 >> 1;
+    e += 1;
+    if (rb && (sticky || (mant & 1))) mant += 1;
+    return ldexp((double)mant, e);
+}
+
+__device__ __forceinline__ ull warp_sum(ull x) {
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// One warp per row of the rank-space CSR.
+__global__ void __launch_bounds__(256)
+k_gather(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
+         const int32_t* __restrict__ col, const int64_t* __restrict__ twin,
+         const uint8_t* __restrict__ flag, const ull* __restrict__ tri,
+         const int32_t* __restrict__ perm, int64_t n, ull den, ull* __restrict__ numer_rank,
+         ull* __restrict__ numer_out, double* __restrict__ tc_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+        const int64_t b = row_ptr[r], h = hstart[r], e = row_ptr[r + 1];
+        ull acc = 0;
+        for (int64_t p = b + lane; p < h; p += 32) {
+            ull w = flag[twin[p]] ? 1ull : 3ull;
+            acc += w * tri[col[p]];
+        }
+        for (int64_t p = h + lane; p < e; p += 32) {
+            ull w = flag[p] ? 1ull : 3ull;
+            acc += w * tri[col[p]];
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            acc += tri[r];
+            numer_rank[r] = acc;
+            const int32_t v = perm[r];
+            if (numer_out) numer_out[v] = acc;
+            if (tc_out) tc_out[v] = div_rn(acc, den);
+        }
+    }
+}
+
+__global__ void k_divide(const ull* __restrict__ numer, int64_t n, ull den, double* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = div_rn(numer[i], den);
+}
+
+__global__ void k_export_tri(const ull* __restrict__ tri, const int32_t* __restrict__ perm,
+                             int64_t n, ull* __restrict__ out) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        out[perm[r]] = tri[r];
+}
+
+__global__ void k_export_flags(const uint8_t* __restrict__ flag, const int64_t* __restrict__ edge_tail,
+                               int64_t m, uint8_t* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = flag[edge_tail[e]];
+}
+
+inline int blocks_for(int64_t items, int threads) {
+    int64_t b = (items + threads - 1) / threads;
+    int64_t cap = (int64_t)sm_count() * 16;
+    if (b < 1) b = 1;
+    return (int)(b < cap ? b : cap);
+}
+
+}  // namespace
+
+tc_status run_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, cudaStream_t s) {
+    const int64_t n = g->n;
+    if (n == 0) return TC_OK;
+    const ull den = 3ull * (ull)g->total;
+    launch_scope ls("gather", s);
+    k_gather<<<blocks_for(n * 32, 256), 256, 0, s>>>(g->row_ptr, g->hstart, g->col, g->twin,
+                                                      g->flag, g->tri, g->perm, n, den, g->numer,
+                                                      (ull*)d_numer, d_tc);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+tc_status run_divide(const uint64_t* d_numer, int64_t n, uint64_t den, double* d_tc, cudaStream_t s) {
+    if (n == 0) return TC_OK;
+    launch_scope ls("divide", s);
+    k_divide<<<blocks_for(n, 256), 256, 0, s>>>((const ull*)d_numer, n, (ull)den, d_tc);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+tc_status export_tri(tc_graph* g, uint64_t* d_tri, cudaStream_t s) {
+    if (g->n == 0) return TC_OK;
+    launch_scope ls("export_tri", s);
+    k_export_tri<<<blocks_for(g->n, 256), 256, 0, s>>>(g->tri, g->perm, g->n, (ull*)d_tri);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+tc_status export_flags(tc_graph* g, uint8_t* d_flag, cudaStream_t s) {
+    if (g->m == 0) return TC_OK;
+    launch_scope ls("export_flags", s);
+    k_export_flags<<<blocks_for(g->m, 256), 256, 0, s>>>(g->flag, g->edge_tail, g->m, d_flag);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+}  // namespace tcx

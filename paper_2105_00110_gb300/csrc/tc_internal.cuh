@@ -1,0 +1,119 @@
+// Internal declarations of the GB300 triangle-centrality library.
+//
+// Device layout of a built graph (all in the degree-ordered label space
+// "rank": rank r is the r-th vertex in the order π of section "Notation",
+// ascending degree, ties by caller label):
+//
+//   row_ptr[n+1]  int64   symmetric CSR offsets, row r = rank r
+//   col[2m]       int32   neighbour ranks, each row ascending, so row r is
+//                         [ N_L(r) | N_H(r) ] with the split at hstart[r]
+//   hstart[n]     int64   first position of N_H(r) in row r
+//   twin[2m]      int64   for a head entry p = (v, u), u < v: the position of
+//                         v inside N_H(u) (row u); unused for tail entries
+//   hrem[2m]      int32   for a head entry: |{w ∈ N_H(u) : w > v}|, the
+//                         length of the part of N_H(u) that can close a
+//                         triangle with the oriented edge u -> v
+//   edge_tail[m]  int64   canonical edge e -> its tail position in rank space
+//   perm[n]       int32   rank -> caller label
+//   edge_u/v[m]   int32   canonical undirected edges, caller labels, u < v,
+//                         sorted by (u, v)
+//
+// Work items of the count step (the planner's output): an item is a middle
+// vertex v and a range [pb, pe) of its head entries (lower neighbours u).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tc.h"
+
+#define TC_WARP_CAP 512          // N_H(v) ids staged per warp item
+#define TC_CTA_THREADS 256
+#define TC_CTA_SMEM (200 * 1024) // dynamic shared memory of a CTA item
+
+struct tc_plan {
+    int64_t n_warp = 0, n_cta = 0;
+    int32_t* w_v = nullptr;      // warp items
+    int64_t* w_pb = nullptr;
+    int64_t* w_pe = nullptr;
+    int32_t* c_v = nullptr;      // CTA items
+    int64_t* c_pb = nullptr;
+    int64_t* c_pe = nullptr;
+};
+
+struct tc_graph {
+    int64_t n = 0, m = 0;
+    int bits = 1;                // bits needed for a label in [0, n)
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    // canonical (caller labels)
+    int32_t* edge_u = nullptr;
+    int32_t* edge_v = nullptr;
+    int32_t* perm = nullptr;
+    // rank space
+    int64_t* row_ptr = nullptr;
+    int32_t* col = nullptr;
+    int64_t* hstart = nullptr;
+    int64_t* twin = nullptr;
+    int32_t* hrem = nullptr;
+    int64_t* edge_tail = nullptr;
+    tc_plan plan;
+    // workspace of tc_count / tc_centrality
+    unsigned long long* tri = nullptr;   // [n], rank space
+    uint8_t* flag = nullptr;             // [2m], meaningful on tail entries
+    unsigned long long* numer = nullptr; // [n], rank space
+    unsigned long long* counters = nullptr;  // [8]: 0 total, 1 warp cursor, 2 cta cursor
+    int counted = 0;
+    uint64_t total = 0;
+    int strategy = TC_STRATEGY_AUTO;
+    tc_graph_stats stats{};
+};
+
+// ---------------------------------------------------------------- helpers
+namespace tcx {
+
+// Status of a CUDA runtime result.
+tc_status from_cuda(cudaError_t e);
+
+// Stream-ordered allocation from the device pool (no implicit sync).
+tc_status dalloc(void** p, size_t bytes, cudaStream_t s);
+void dfree(void* p, cudaStream_t s);
+
+// Launch accounting and optional per-kernel event timing.
+void note_launch(const char* name, cudaStream_t s, int phase);  // phase 0 before, 1 after
+struct launch_scope {
+    const char* name; cudaStream_t s;
+    launch_scope(const char* n, cudaStream_t st) : name(n), s(st) { note_launch(name, s, 0); }
+    ~launch_scope() { note_launch(name, s, 1); }
+};
+
+int sm_count();
+
+// build pieces (tc_build.cu)
+tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np, int64_t n,
+                      uint32_t flags, cudaStream_t s);
+void free_graph_memory(tc_graph* g);
+
+// count (tc_count.cu)
+tc_status run_count(tc_graph* g, cudaStream_t s);
+// gather + divide (tc_gather.cu)
+tc_status run_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, cudaStream_t s);
+tc_status run_divide(const uint64_t* d_numer, int64_t n, uint64_t den, double* d_tc, cudaStream_t s);
+tc_status export_tri(tc_graph* g, uint64_t* d_tri, cudaStream_t s);
+tc_status export_flags(tc_graph* g, uint8_t* d_flag, cudaStream_t s);
+
+}  // namespace tcx
+
+#define TC_TRY(expr)                                    \
+    do {                                                \
+        tc_status _st = (expr);                         \
+        if (_st < 0) return _st;                        \
+    } while (0)
+
+#define TC_CUDA(expr)                                   \
+    do {                                                \
+        cudaError_t _e = (expr);                        \
+        if (_e != cudaSuccess) return tcx::from_cuda(_e); \
+    } while (0)
+
+#define TC_LAUNCH_CHECK() TC_CUDA(cudaGetLastError())

@@ -1,0 +1,191 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle,
+element by element.  Counts, flags and numerators must be bit-exact and TC
+must be the same binary64 value (both sides round the same exact rational
+once, to nearest-even), i.e. 0 ulp where north of the 1-ulp bound."""
+from __future__ import annotations
+
+import random
+
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+import paper_2105_00110_gb300 as tcg
+from golden_io import fixtures, load
+
+pytestmark = pytest.mark.gpu
+
+STRATS = ["auto", "bsearch", "merge", "bitmap"]
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built():
+    tcg.build()
+    torch.cuda.init()
+
+
+def gpu_run(src, dst, n, strategy=None, ids=np.int32, on_device=True):
+    s = torch.from_numpy(np.ascontiguousarray(src).astype(ids))
+    d = torch.from_numpy(np.ascontiguousarray(dst).astype(ids))
+    if on_device:
+        s, d = s.cuda(), d.cuda()
+    res = tcg.triangle_centrality(s, d, n, strategy=strategy)
+    torch.cuda.synchronize()
+    out = {}
+    for k, v in res.items():
+        out[k] = v.cpu().numpy() if isinstance(v, torch.Tensor) else v
+    return out
+
+
+def assert_parity(res, ref, n):
+    assert res["n"] == n
+    assert res["total"] == ref["total"]
+    assert res["den"] == ref["den"]
+    ptr, adj = ref["ptr"], ref["adj"]
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(ptr))
+    keep = adj > rows
+    assert res["m"] == int(keep.sum())
+    np.testing.assert_array_equal(res["edge_u"], rows[keep])
+    np.testing.assert_array_equal(res["edge_v"], adj[keep])
+    np.testing.assert_array_equal(res["tri"], ref["tri"])
+    np.testing.assert_array_equal(res["flag"], ref["flag"][keep])
+    np.testing.assert_array_equal(res["numer"], ref["numer"])
+    if ref["total"] == 0:
+        assert res["status"] == tcg.TC_NO_TRIANGLES
+        assert np.all(np.isnan(res["tc"]))
+    else:
+        assert res["status"] == tcg.TC_OK
+        # identical binary64 values (0 ulp)
+        np.testing.assert_array_equal(res["tc"].view(np.uint64), ref["tc"].view(np.uint64))
+
+
+def check(src, dst, n, strategy=None, mode="definition", **kw):
+    ref = oracle.run(src, dst, n, mode)
+    res = gpu_run(src, dst, n, strategy, **kw)
+    assert_parity(res, ref, n)
+    return res, ref
+
+
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("name", fixtures())
+def test_golden(name, strategy):
+    src, dst, n, _, _ = load(name)
+    check(src, dst, n, strategy)
+
+
+@pytest.mark.parametrize("strategy", STRATS)
+def test_closed_forms(strategy):
+    for k in (3, 4, 40, 300, 600):
+        check(*gg.complete_graph(k), strategy=strategy)
+    check(*gg.bridge_to_cliques(5, 6), strategy=strategy)
+    check(*gg.disjoint_cliques(4, 7), strategy=strategy)
+    s, d, n, _, _ = gg.clique_chain(6, 5)
+    check(s, d, n, strategy)
+    s, d, n, _, _ = gg.clique_chain(5, 4, ring=True)
+    check(s, d, n, strategy)
+    check(*gg.single_triangle_with_pendants(3), strategy=strategy)
+
+
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("seed", range(4))
+def test_gnp(seed, strategy):
+    rnd = random.Random(100 + seed)
+    n = rnd.randint(20, 160)
+    p = rnd.choice([0.02, 0.1, 0.3, 0.7])
+    check(*gg.gnp(n, p, seed), strategy=strategy)
+
+
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("scale", [8, 10, 12])
+def test_rmat(scale, strategy):
+    seed = 0x5EED0000 if scale == 12 else 0x5EED0000 + scale
+    check(*gg.rmat(scale, seed=seed), strategy=strategy)
+
+
+@pytest.mark.parametrize("ids,on_device", [(np.int64, False), (np.int64, True), (np.int32, False)])
+def test_input_forms(ids, on_device):
+    s, d, n = gg.rmat(9, seed=0x5EED0009)
+    check(s, d, n, ids=ids, on_device=on_device)
+
+
+@pytest.mark.parametrize("strategy", STRATS)
+def test_rmat16_many_tiles(strategy):
+    # hubs become CTA items; several items per hub; oracle in degree-ordered mode
+    s, d, n = gg.rmat(16, seed=0x5EED0010)
+    res, _ = check(s, d, n, strategy, mode="fast")
+    assert res["stats"]["items_cta"] > 0 and res["stats"]["items_warp"] > 0
+
+
+def test_grid_chung_lu_small():
+    for strategy in STRATS:
+        check(*gg.grid_chung_lu(side=96, seed=0x5EED0002), strategy=strategy)
+
+
+def test_batched_shapes():
+    check(*gg.barabasi_albert(3000, 5, seed=31))
+    check(*gg.planted_hierarchy(2000, 20, 8, 0.01, seed=32))
+
+
+def test_edge_cases():
+    e = np.zeros(0, np.int32)
+    r = gpu_run(e, e, 0)
+    assert r["n"] == 0 and r["m"] == 0 and r["total"] == 0
+    r = gpu_run(e, e, 7)
+    assert r["m"] == 0 and np.all(r["tri"] == 0) and np.all(np.isnan(r["tc"]))
+    # self-loops and duplicates only
+    check(np.array([1, 1, 2, 2, 2], np.int32), np.array([1, 2, 1, 2, 1], np.int32), 4)
+    # a tree: triangle-free, explicit status
+    src = np.arange(1, 50, dtype=np.int32)
+    dst = (np.arange(1, 50) // 2).astype(np.int32)
+    res, _ = check(src, dst, 50)
+    assert res["status"] == tcg.TC_NO_TRIANGLES
+    # one triangle plus isolated vertices
+    check(np.array([0, 1, 2], np.int32), np.array([1, 2, 0], np.int32), 10)
+
+
+def test_invalid_ids_rejected():
+    for bad in ([0, 5], [-1, 2]):
+        with pytest.raises(tcg.TCError) as ei:
+            gpu_run(np.array(bad, np.int32), np.array([1, 1], np.int32), 5)
+        assert ei.value.status == tcg.TC_ERR_INVALID_ARG
+
+
+def test_call_order():
+    g = tcg.Graph(torch.tensor([0, 1], dtype=torch.int32, device="cuda"),
+                  torch.tensor([1, 2], dtype=torch.int32, device="cuda"), 3)
+    with pytest.raises(tcg.TCError) as ei:
+        g.centrality()
+    assert ei.value.status == tcg.TC_ERR_STATE
+    g.close()
+
+
+def test_divide_exact():
+    rnd = random.Random(9)
+    num, dens = [], []
+    for _ in range(4000):
+        b = rnd.choice([rnd.randint(1, 2**53 - 1), rnd.randint(2**53, 2**64 - 1), rnd.randint(1, 2**64 - 1)])
+        a = rnd.randint(0, b)
+        num.append(a)
+        dens.append(b)
+    for den in sorted(set(dens))[:40] + [2**64 - 1, 3, 2**53 + 1, 0]:
+        a = np.array([x % (den + 1) if den else x for x in num[:512]] + [0, den], dtype=np.uint64)
+        t = torch.from_numpy(a).cuda()
+        out = torch.empty(len(a), dtype=torch.float64, device="cuda")
+        tcg.tc_divide(t, den, out)
+        got = out.cpu().numpy()
+        want = np.array([oracle.div_rn(int(x), den) for x in a])
+        np.testing.assert_array_equal(got.view(np.uint64), want.view(np.uint64))
+
+
+def test_repeatable_and_relabel_invariant():
+    s, d, n = gg.rmat(11, seed=0x5EED000B)
+    a = gpu_run(s, d, n)
+    b = gpu_run(s, d, n)
+    for k in ("tri", "numer", "tc", "flag"):
+        np.testing.assert_array_equal(a[k], b[k])
+    ps, pd, perm = gg.permute_labels(s, d, n, seed=5)
+    c = gpu_run(ps, pd, n)
+    np.testing.assert_array_equal(c["tri"][perm], a["tri"])
+    np.testing.assert_array_equal(c["numer"][perm], a["numer"])
