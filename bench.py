@@ -111,6 +111,20 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def aggregate(t_ms: float, e2e_ms: float, units: int, e2e_units: int, world: int, device=None):
+    """Whole-job figures across ranks: the slowest rank's time (MAX) and the
+    units all ranks processed (SUM).  Identity for a single process."""
+    if world <= 1:
+        return t_ms, e2e_ms, units, e2e_units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_ms, e2e_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units), float(e2e_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), int(u[0]), int(u[1])
+
+
 # ------------------------------------------------------------ our path
 def run_ours(args, spec, wl_name):
     import numpy as np
@@ -206,15 +220,7 @@ def run_ours(args, spec, wl_name):
     barrier()
     e2e_ms = e0.elapsed_time(e1)
 
-    t_max, e2e_max = t_ms, e2e_ms
-    edges_all, e2e_edges_all = edges, e2e_edges
-    if world > 1:
-        agg = torch.tensor([t_ms, e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(agg, op=dist.ReduceOp.MAX)
-        cnt = torch.tensor([edges, e2e_edges], dtype=torch.float64, device=dev)
-        dist.all_reduce(cnt, op=dist.ReduceOp.SUM)
-        t_max, e2e_max = float(agg[0]), float(agg[1])
-        edges_all, e2e_edges_all = int(cnt[0]), int(cnt[1])
+    t_max, e2e_max, edges_all, e2e_edges_all = aggregate(t_ms, e2e_ms, edges, e2e_edges, world, dev)
 
     if rank == 0:
         peak, peak_kind = peaks()

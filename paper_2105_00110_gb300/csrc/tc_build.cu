@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "tc_internal.cuh"
 
@@ -249,18 +250,20 @@ int bits_for(int64_t n) {
 // Owns every temporary of a build so that an early return releases them.
 struct scratch {
     cudaStream_t s;
-    void* p[16] = {};
-    int k = 0;
-    explicit scratch(cudaStream_t st) : s(st) {}
+    std::vector<void*> p;
+    explicit scratch(cudaStream_t st) : s(st) { p.reserve(64); }
     template <typename T>
     tc_status get(T** out, size_t count) {
         void* q = nullptr;
+        *out = nullptr;
         TC_TRY(dalloc(&q, count * sizeof(T) + 16, s));
-        p[k++] = q;
+        p.push_back(q);
         *out = (T*)q;
         return TC_OK;
     }
-    ~scratch() { for (int i = 0; i < k; ++i) dfree(p[i], s); }
+    ~scratch() {
+        for (void* q : p) dfree(q, s);
+    }
 };
 
 template <typename T>
