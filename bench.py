@@ -227,8 +227,8 @@ def run_ours(args, spec, wl_name):
         # the dominant kernel of the step and its algorithmic bytes per launch
         kern = {k: v for k, v in prof.items()}
         top = max(kern.items(), key=lambda kv: kv[1][1]) if kern else None
-        bytes_per = {"count_warp": stats["count_bytes_warp"], "count_cta": stats["count_bytes_cta"],
-                     "gather": stats["centrality_bytes"]}
+        bytes_per = {name: stats["class_bytes"][c] for name, c in tcg.KERNEL_CLASS.items()}
+        bytes_per["gather"] = stats["centrality_bytes"]
         roof = None
         if top and top[0] in bytes_per:
             name, (launch_n, tot_ms) = top

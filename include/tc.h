@@ -74,6 +74,8 @@ typedef enum {
 #define TC_STRATEGY_MERGE   2   /* warp-cooperative merge-path intersection of two sorted lists         */
 #define TC_STRATEGY_BITMAP  3   /* N_H(v) as a shared-memory bitmap over its id window (falls back to
                                    BSEARCH for an item whose window does not fit)                       */
+#define TC_STRATEGY_GLOBAL  4   /* binary search of N_H(v) in place in global memory (what lists too
+                                   long for shared memory use under every other strategy)              */
 
 /*
  * Build the simple undirected graph G from `num_pairs` pairs (src[i],
@@ -166,10 +168,10 @@ typedef struct {
     double  sum_out_degree_sq;   /* Σ_v |N_H(v)|²                                       */
     double  wedges;              /* Σ_v C(|N_H(v)|, 2): ids streamed by the count step   */
     double  avg_degeneracy;      /* δ̄ = (1/m) Σ_{(v,u)∈E} min(d(v), d(u))              */
-    int64_t items_warp, items_cta;     /* work items of the count step per granularity */
-    double  count_bytes;         /* algorithmic DRAM bytes of the count step            */
-    double  count_bytes_warp;    /*   ... of its warp-item kernel                        */
-    double  count_bytes_cta;     /*   ... of its CTA-item kernel                         */
+    int64_t items[4];            /* count-step work items per class: bitmap (small shared
+                                    footprint), bitmap (large), warp list, CTA list     */
+    double  class_bytes[4];      /* algorithmic DRAM bytes of each class's kernel       */
+    double  count_bytes;         /* algorithmic DRAM bytes of the whole count step      */
     double  centrality_bytes;    /* algorithmic DRAM bytes of the gather + divide step  */
 } tc_graph_stats;
 
@@ -194,6 +196,8 @@ tc_status tc_profile_read(tc_kernel_time* out, int cap, int* count);
 /* Number of kernels this library has launched since load (all threads). */
 int64_t tc_launch_count(void);
 
+/* Releases g.  Its device memory is freed in stream order on the stream of
+ * the last call made on g, which must still exist. */
 void tc_graph_free(tc_graph* g);
 const char* tc_status_str(tc_status s);
 

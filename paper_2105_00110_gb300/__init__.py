@@ -35,7 +35,8 @@ TC_STRATEGY_AUTO = 0
 TC_STRATEGY_BSEARCH = 1
 TC_STRATEGY_MERGE = 2
 TC_STRATEGY_BITMAP = 3
-STRATEGIES = {"auto": 0, "bsearch": 1, "merge": 2, "bitmap": 3}
+TC_STRATEGY_GLOBAL = 4
+STRATEGIES = {"auto": 0, "bsearch": 1, "merge": 2, "bitmap": 3, "global": 4}
 
 EXPORTED = ["tc_build_csr", "tc_count", "tc_centrality", "tc_divide", "tc_graph_info",
             "tc_copy_edges", "tc_get_stats", "tc_set_strategy", "tc_profile_enable",
@@ -54,12 +55,21 @@ class GraphStats(ctypes.Structure):
                 ("max_degree", ctypes.c_int64), ("max_out_degree", ctypes.c_int64),
                 ("sum_out_degree_sq", ctypes.c_double), ("wedges", ctypes.c_double),
                 ("avg_degeneracy", ctypes.c_double),
-                ("items_warp", ctypes.c_int64), ("items_cta", ctypes.c_int64),
-                ("count_bytes", ctypes.c_double), ("count_bytes_warp", ctypes.c_double),
-                ("count_bytes_cta", ctypes.c_double), ("centrality_bytes", ctypes.c_double)]
+                ("items", ctypes.c_int64 * 4), ("class_bytes", ctypes.c_double * 4),
+                ("count_bytes", ctypes.c_double), ("centrality_bytes", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if not isinstance(v, (int, float)) else v
+        return d
+
+
+CLASS_NAMES = ["bitmap_s", "bitmap_l", "warp", "cta_list"]
+# kernel name (as reported by tc_profile_read) -> item class
+KERNEL_CLASS = {"count_bitmap_s": 0, "count_bitmap_l": 1, "count_warp": 2,
+                "count_cta_list": 3, "count_cta_global": 3}
 
 
 class KernelTime(ctypes.Structure):

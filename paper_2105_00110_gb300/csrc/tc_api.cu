@@ -235,7 +235,7 @@ tc_status tc_get_stats(const tc_graph* g, tc_graph_stats* out) {
 }
 
 tc_status tc_set_strategy(tc_graph* g, int strategy) {
-    if (!g || strategy < TC_STRATEGY_AUTO || strategy > TC_STRATEGY_BITMAP) return TC_ERR_INVALID_ARG;
+    if (!g || strategy < TC_STRATEGY_AUTO || strategy > TC_STRATEGY_GLOBAL) return TC_ERR_INVALID_ARG;
     g->strategy = strategy;
     return TC_OK;
 }

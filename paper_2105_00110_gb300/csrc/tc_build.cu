@@ -146,59 +146,32 @@ __global__ void k_twin(const uint64_t* __restrict__ keys, const uint32_t* __rest
     }
 }
 
-// ----------------------------------------------------------------- planner
-struct plan_params {
-    int64_t warp_cap;      // max |N_H(v)| of a warp item
-    int64_t cta_min_work;  // W(v) at or above which v becomes CTA items
-    int64_t cta_chunk;     // target work of one CTA item
-};
-
-struct plan_stats {
+// ------------------------------------------------------------ row work
+struct row_stats {
     unsigned long long sum_h2, wedges, sum_dh, max_h, max_d;
-    unsigned long long cta_wedges, cta_head, cta_staged, cta_vertices;
 };
 
-// One warp per row: W(v), item counts (written in reverse rank order so
-// that the heaviest vertices come first), shape statistics.
-__global__ void k_plan_rows(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
-                            const int32_t* __restrict__ hrem, int64_t n, plan_params pp,
-                            int64_t* __restrict__ nw, int64_t* __restrict__ nc,
-                            int64_t* __restrict__ work, plan_stats* __restrict__ st) {
+// One warp per row: W(v) = Σ_{u ∈ N_L(v)} hrem(u, v), the number of ids the
+// count step streams for middle vertex v; plus shape statistics.
+__global__ void k_row_work(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
+                           const int32_t* __restrict__ hrem, int64_t n, int64_t* __restrict__ work,
+                           row_stats* __restrict__ st) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     unsigned long long l_h2 = 0, l_w = 0, l_dh = 0, l_maxh = 0, l_maxd = 0;
-    unsigned long long c_w = 0, c_head = 0, c_staged = 0, c_v = 0;
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
-        int64_t b = row_ptr[r], h = hstart[r], e = row_ptr[r + 1];
+        const int64_t b = row_ptr[r], h = hstart[r], e = row_ptr[r + 1];
         unsigned long long w = 0;
         for (int64_t p = b + lane; p < h; p += 32) w += (unsigned long long)hrem[p];
         for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
         if (lane == 0) {
-            int64_t hv = e - h, lv = h - b;
-            int64_t cw = 0, cc = 0;
-            if (w > 0 && hv > 0) {
-                if (hv > pp.warp_cap || (int64_t)w >= pp.cta_min_work) {
-                    cc = ((int64_t)w + pp.cta_chunk - 1) / pp.cta_chunk;
-                    if (cc > lv) cc = lv;
-                    if (cc < 1) cc = 1;
-                } else {
-                    cw = 1;
-                }
-            }
-            if (cc) {
-                c_w += w;
-                c_head += (unsigned long long)lv;
-                c_staged += (unsigned long long)hv;
-                c_v += 1;
-            }
-            nw[n - 1 - r] = cw;
-            nc[n - 1 - r] = cc;
+            const unsigned long long hv = (unsigned long long)(e - h), d = (unsigned long long)(e - b);
             work[r] = (int64_t)w;
-            l_h2 += (unsigned long long)(hv * hv);
+            l_h2 += hv * hv;
             l_w += w;
-            l_dh += (unsigned long long)((e - b) * hv);
-            l_maxh = l_maxh > (unsigned long long)hv ? l_maxh : (unsigned long long)hv;
-            l_maxd = l_maxd > (unsigned long long)(e - b) ? l_maxd : (unsigned long long)(e - b);
+            l_dh += d * hv;
+            l_maxh = l_maxh > hv ? l_maxh : hv;
+            l_maxd = l_maxd > d ? l_maxd : d;
         }
     }
     if (lane == 0) {
@@ -207,37 +180,6 @@ __global__ void k_plan_rows(const int64_t* __restrict__ row_ptr, const int64_t* 
         atomicAdd(&st->sum_dh, l_dh);
         atomicMax(&st->max_h, l_maxh);
         atomicMax(&st->max_d, l_maxd);
-        atomicAdd(&st->cta_wedges, c_w);
-        atomicAdd(&st->cta_head, c_head);
-        atomicAdd(&st->cta_staged, c_staged);
-        atomicAdd(&st->cta_vertices, c_v);
-    }
-}
-
-__global__ void k_plan_emit(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
-                            int64_t n, const int64_t* __restrict__ nw, const int64_t* __restrict__ nc,
-                            const int64_t* __restrict__ ow, const int64_t* __restrict__ oc,
-                            int32_t* __restrict__ w_v, int64_t* __restrict__ w_pb,
-                            int64_t* __restrict__ w_pe, int32_t* __restrict__ c_v,
-                            int64_t* __restrict__ c_pb, int64_t* __restrict__ c_pe) {
-    GRID_STRIDE(i, n) {
-        int64_t r = n - 1 - i;
-        int64_t b = row_ptr[r], h = hstart[r];
-        if (nw[i]) {
-            int64_t o = ow[i];
-            w_v[o] = (int32_t)r;
-            w_pb[o] = b;
-            w_pe[o] = h;
-        }
-        int64_t k = nc[i];
-        if (k) {
-            int64_t o = oc[i], lv = h - b;
-            for (int64_t c = 0; c < k; ++c) {
-                c_v[o + c] = (int32_t)r;
-                c_pb[o + c] = b + lv * c / k;
-                c_pe[o + c] = b + lv * (c + 1) / k;
-            }
-        }
     }
 }
 
@@ -281,10 +223,9 @@ tc_status sort_keys(scratch& sc, cub::DoubleBuffer<T>& buf, int64_t count, int e
 void free_graph_memory(tc_graph* g) {
     cudaStream_t s = g->stream;
     void* ptrs[] = {g->edge_u, g->edge_v, g->perm, g->row_ptr, g->col, g->hstart, g->twin,
-                    g->hrem, g->edge_tail, g->plan.w_v, g->plan.w_pb, g->plan.w_pe,
-                    g->plan.c_v, g->plan.c_pb, g->plan.c_pe, g->tri, g->flag, g->numer,
-                    g->counters};
+                    g->hrem, g->edge_tail, g->work, g->tri, g->flag, g->numer, g->counters};
     for (void* q : ptrs) dfree(q, s);
+    free_plan(g->plan, s);
 }
 
 tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np, int64_t n,
@@ -466,60 +407,21 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
         TC_LAUNCH_CHECK();
     }
 
-    // ---- 6. planner
-    plan_params pp{TC_WARP_CAP, 32768, 65536};
-    int64_t *nw = nullptr, *nc = nullptr, *ow = nullptr, *oc = nullptr, *work = nullptr;
-    plan_stats* dst_stats = nullptr;
-    TC_TRY(sc.get(&nw, n + 1));
-    TC_TRY(sc.get(&nc, n + 1));
-    TC_TRY(sc.get(&ow, n + 1));
-    TC_TRY(sc.get(&oc, n + 1));
-    TC_TRY(sc.get(&work, n + 1));
+    // ---- 6. per-row work, statistics and the count-step plan
+    TC_TRY(dalloc((void**)&g->work, (n + 1) * 8, s));
+    row_stats* dst_stats = nullptr;
     TC_TRY(sc.get(&dst_stats, 1));
-    TC_CUDA(cudaMemsetAsync(dst_stats, 0, sizeof(plan_stats), s));
-    TC_CUDA(cudaMemsetAsync(nw, 0, (n + 1) * 8, s));
-    TC_CUDA(cudaMemsetAsync(nc, 0, (n + 1) * 8, s));
+    TC_CUDA(cudaMemsetAsync(dst_stats, 0, sizeof(row_stats), s));
     if (n > 0) {
-        launch_scope ls("plan_rows", s);
-        int64_t warps = (n + 0);
-        int blocks = (int)std::min<int64_t>((warps * 32 + kThreads - 1) / kThreads,
-                                            (int64_t)sm_count() * 16);
-        k_plan_rows<<<std::max(blocks, 1), kThreads, 0, s>>>(g->row_ptr, g->hstart, g->hrem, n, pp,
-                                                             nw, nc, work, dst_stats);
+        launch_scope ls("build_row_work", s);
+        int blocks = (int)std::min<int64_t>((n * 32 + kThreads - 1) / kThreads, (int64_t)sm_count() * 16);
+        k_row_work<<<std::max(blocks, 1), kThreads, 0, s>>>(g->row_ptr, g->hstart, g->hrem, n, g->work,
+                                                            dst_stats);
         TC_LAUNCH_CHECK();
     }
-    {
-        size_t bytes = 0;
-        TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, nw, ow, n + 1, s));
-        uint8_t* tmp = nullptr;
-        TC_TRY(sc.get(&tmp, bytes));
-        launch_scope ls("plan_scan", s);
-        TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, bytes, nw, ow, n + 1, s));
-        TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, bytes, nc, oc, n + 1, s));
-    }
-    int64_t counts[2] = {0, 0};
-    plan_stats hst{};
-    TC_CUDA(cudaMemcpyAsync(&counts[0], ow + n, 8, cudaMemcpyDeviceToHost, s));
-    TC_CUDA(cudaMemcpyAsync(&counts[1], oc + n, 8, cudaMemcpyDeviceToHost, s));
-    TC_CUDA(cudaMemcpyAsync(&hst, dst_stats, sizeof(plan_stats), cudaMemcpyDeviceToHost, s));
+    row_stats hst{};
+    TC_CUDA(cudaMemcpyAsync(&hst, dst_stats, sizeof(row_stats), cudaMemcpyDeviceToHost, s));
     TC_CUDA(cudaStreamSynchronize(s));
-    g->plan.n_warp = counts[0];
-    g->plan.n_cta = counts[1];
-    TC_TRY(dalloc((void**)&g->plan.w_v, (counts[0] + 1) * 4, s));
-    TC_TRY(dalloc((void**)&g->plan.w_pb, (counts[0] + 1) * 8, s));
-    TC_TRY(dalloc((void**)&g->plan.w_pe, (counts[0] + 1) * 8, s));
-    TC_TRY(dalloc((void**)&g->plan.c_v, (counts[1] + 1) * 4, s));
-    TC_TRY(dalloc((void**)&g->plan.c_pb, (counts[1] + 1) * 8, s));
-    TC_TRY(dalloc((void**)&g->plan.c_pe, (counts[1] + 1) * 8, s));
-    if (n > 0 && counts[0] + counts[1] > 0) {
-        launch_scope ls("plan_emit", s);
-        k_plan_emit<<<grid_for(n), kThreads, 0, s>>>(g->row_ptr, g->hstart, n, nw, nc, ow, oc,
-                                                     g->plan.w_v, g->plan.w_pb, g->plan.w_pe,
-                                                     g->plan.c_v, g->plan.c_pb, g->plan.c_pe);
-        TC_LAUNCH_CHECK();
-    }
-
-    // ---- statistics (host)
     tc_graph_stats& S = g->stats;
     S.n = n;
     S.m = m;
@@ -528,25 +430,16 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
     S.sum_out_degree_sq = (double)hst.sum_h2;
     S.wedges = (double)hst.wedges;
     S.avg_degeneracy = m ? (double)hst.sum_dh / (double)m : 0.0;
-    S.items_warp = counts[0];
-    S.items_cta = counts[1];
     // Count step: stage N_H(v) once per middle vertex (4m), read each head
-    // entry's label, twin and hrem (16m), stream every wedge id (4 W), write
-    // the vertex counts (8n) and one flag byte per tail entry (m).
+    // entry's label, twin and stream length (16m), stream every wedge id
+    // (4 W), write the vertex counts (8n) and one flag byte per tail entry (m).
     S.count_bytes = 4.0 * m + 16.0 * m + 4.0 * S.wedges + 8.0 * n + 1.0 * m;
-    {
-        // split by kernel: the CTA-item kernel stages N_H(v) of the heavy
-        // vertices, reads their head entries and streams their wedges; the
-        // warp-item kernel does the rest, including the count and flag writes
-        double cw = (double)hst.cta_wedges, ch = (double)hst.cta_head, chv = (double)hst.cta_staged;
-        S.count_bytes_cta = 4.0 * chv + 16.0 * ch + 4.0 * cw;
-        S.count_bytes_warp = S.count_bytes - S.count_bytes_cta;
-    }
     // Gather: per vertex row_ptr, hstart, perm, △(v), numerator and TC out
     // (8+8+4+8+8+8); per adjacency entry its label and the neighbour's count
     // (4+8); per head entry twin and the mirrored flag (8+1); per tail entry
     // its flag (1).
     S.centrality_bytes = 44.0 * n + 12.0 * (double)e2 + 9.0 * m + 1.0 * m;
+    TC_TRY(make_plan(g, g->strategy, s));
     TC_CUDA(cudaStreamSynchronize(s));
     return TC_OK;
 }

@@ -29,16 +29,23 @@
 
 #define TC_WARP_CAP 512          // N_H(v) ids staged per warp item
 #define TC_CTA_THREADS 256
-#define TC_CTA_SMEM (200 * 1024) // dynamic shared memory of a CTA item
+
+// Item classes of the count step.
+enum tc_item_class {
+    TC_CLS_BITMAP_S = 0,   // CTA, N_H(v) as a bitmap over its id window, small shared footprint
+    TC_CLS_BITMAP_L = 1,   // CTA, bitmap with a large shared footprint
+    TC_CLS_WARP = 2,       // warp, N_H(v) as a sorted list (binary search or merge)
+    TC_CLS_CTA_LIST = 3,   // CTA, sorted list in shared memory (or global if it does not fit)
+    TC_NUM_CLS = 4
+};
 
 struct tc_plan {
-    int64_t n_warp = 0, n_cta = 0;
-    int32_t* w_v = nullptr;      // warp items
-    int64_t* w_pb = nullptr;
-    int64_t* w_pe = nullptr;
-    int32_t* c_v = nullptr;      // CTA items
-    int64_t* c_pb = nullptr;
-    int64_t* c_pe = nullptr;
+    int strategy = -1;                 // strategy the plan was made for
+    int64_t count[TC_NUM_CLS] = {};
+    int32_t* v[TC_NUM_CLS] = {};       // middle vertex of each item
+    int64_t* pb[TC_NUM_CLS] = {};      // head-entry range [pb, pe) of the item
+    int64_t* pe[TC_NUM_CLS] = {};
+    size_t smem[TC_NUM_CLS] = {};      // dynamic shared memory of the class's kernel
 };
 
 struct tc_graph {
@@ -57,6 +64,7 @@ struct tc_graph {
     int64_t* twin = nullptr;
     int32_t* hrem = nullptr;
     int64_t* edge_tail = nullptr;
+    int64_t* work = nullptr;             // [n] W(v) = Σ_{u ∈ N_L(v)} hrem(u, v)
     tc_plan plan;
     // workspace of tc_count / tc_centrality
     unsigned long long* tri = nullptr;   // [n], rank space
@@ -95,6 +103,8 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
 void free_graph_memory(tc_graph* g);
 
 // count (tc_count.cu)
+tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s);
+void free_plan(tc_plan& p, cudaStream_t s);
 tc_status run_count(tc_graph* g, cudaStream_t s);
 // gather + divide (tc_gather.cu)
 tc_status run_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, cudaStream_t s);

@@ -17,7 +17,7 @@ from golden_io import fixtures, load
 
 pytestmark = pytest.mark.gpu
 
-STRATS = ["auto", "bsearch", "merge", "bitmap"]
+STRATS = ["auto", "bsearch", "merge", "bitmap", "global"]
 
 
 @pytest.fixture(scope="session", autouse=True)
@@ -115,7 +115,14 @@ def test_rmat16_many_tiles(strategy):
     # hubs become CTA items; several items per hub; oracle in degree-ordered mode
     s, d, n = gg.rmat(16, seed=0x5EED0010)
     res, _ = check(s, d, n, strategy, mode="fast")
-    assert res["stats"]["items_cta"] > 0 and res["stats"]["items_warp"] > 0
+    items = res["stats"]["items"]
+    assert sum(items) > 0
+    if strategy == "auto":
+        assert items[0] > 0 and items[2] > 0     # both bitmap and warp-list items
+    if strategy in ("bsearch", "merge"):
+        assert items[0] == items[1] == 0 and items[2] > 0
+    if strategy == "global":
+        assert items[3] == sum(items)
 
 
 def test_grid_chung_lu_small():
