@@ -538,7 +538,8 @@ template <class K>
 tc_status launch_persistent(K kernel, const char* name, size_t smem, int64_t items, cudaStream_t s,
                             const tc_graph* g, const tc_plan& p, int c, ull* cursor) {
     if (items == 0) return TC_OK;
-    if (smem > 48 * 1024) TC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // static + dynamic shared memory may exceed the 48 KB default
+    if (smem > 0) TC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, TC_CTA_THREADS, smem));
     per_sm = std::max(per_sm, 1);
