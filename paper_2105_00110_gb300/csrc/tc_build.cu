@@ -430,6 +430,9 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
     S.sum_out_degree_sq = (double)hst.sum_h2;
     S.wedges = (double)hst.wedges;
     S.avg_degeneracy = m ? (double)hst.sum_dh / (double)m : 0.0;
+    // the count kernels keep stream lengths and staged indices in 16 bits;
+    // |N_H(v)| <= sqrt(2m) makes this reachable only with m >= 2^31 edges
+    if (S.max_out_degree >= 65536) return TC_ERR_INVALID_ARG;
     // Count step: stage N_H(v) once per middle vertex (4m), read each head
     // entry's label, twin and stream length (16m), stream every wedge id
     // (4 W), write the vertex counts (8n) and one flag byte per tail entry (m).

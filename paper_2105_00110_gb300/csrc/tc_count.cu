@@ -44,27 +44,29 @@ constexpr int kIlp = 4;                 // 32-id windows in flight per lane
 constexpr int kCtaWarps = TC_CTA_THREADS / 32;
 
 // Planner constants.
-constexpr int64_t kBitmapSmallSmem = 44 * 1024;   // dynamic smem of the small-bitmap kernel
-constexpr int64_t kBitmapLargeSmem = 180 * 1024;  // ... of the large-bitmap / CTA-list kernels
+constexpr int64_t kBitmapSmallSmem = 34 * 1024;   // dynamic smem of the small-bitmap CTA kernel (5 CTAs per SM)
+constexpr int64_t kBitmapLargeSmem = 100 * 1024;  // ... of the large-bitmap CTA kernel
+constexpr int64_t kCtaListSmem = 100 * 1024;      // ... of the CTA sorted-list kernel
 constexpr int64_t kCtaChunk = 65536;              // target wedges per CTA item
-constexpr int64_t kWarpChunk = 32768;             // target wedges per warp item
+constexpr int64_t kWarpChunk = 16384;             // target wedges per warp item
 constexpr int64_t kCtaMinWork = 4096;             // below this a vertex is a warp item
 
 enum { L_BITMAP = 0, L_SORTED = 1, L_GLOBAL = 2 };
 
 // ------------------------------------------------------------ lookups
 // N_H(v) as a bitmap over [base, base + nbits): bit (w - base) set iff
-// w ∈ N_H(v); rank[k] = set bits before word k gives w's staged index.
+// w ∈ N_H(v); rank[k] = set bits before word k (16 bits suffice since
+// |N_H(v)| <= sqrt(2m) < 2^16) gives w's staged index.
 struct lookup_bitmap {
     const uint32_t* bits;
-    const uint32_t* rank;
+    const uint16_t* rank;
     int32_t base;
     int32_t nbits;
     __device__ __forceinline__ bool find(int32_t w, int& l) const {
-        uint32_t off = (uint32_t)(w - base);
+        const uint32_t off = (uint32_t)(w - base);
         if (off >= (uint32_t)nbits) return false;
-        uint32_t word = bits[off >> 5];
-        uint32_t bit = 1u << (off & 31);
+        const uint32_t word = bits[off >> 5];
+        const uint32_t bit = 1u << (off & 31);
         if (!(word & bit)) return false;
         l = (int)rank[off >> 5] + __popc(word & (bit - 1));
         return true;
@@ -78,7 +80,7 @@ struct lookup_sorted {
     __device__ __forceinline__ bool find(int32_t w, int& l) const {
         int lo = 0, len = hv;
         while (len > 0) {
-            int half = len >> 1;
+            const int half = len >> 1;
             if (ids[lo + half] < w) {
                 lo += half + 1;
                 len -= half + 1;
@@ -98,7 +100,7 @@ struct lookup_global {
     __device__ __forceinline__ bool find(int32_t w, int& l) const {
         int lo = 0, len = hv;
         while (len > 0) {
-            int half = len >> 1;
+            const int half = len >> 1;
             if (__ldg(ids + lo + half) < w) {
                 lo += half + 1;
                 len -= half + 1;
@@ -111,43 +113,78 @@ struct lookup_global {
     }
 };
 
+// Shared bytes of a bitmap staging: bits, 16-bit ranks, per-id counters.
+__host__ __device__ __forceinline__ int64_t bitmap_bytes(int64_t words, int64_t hv) {
+    return 4 * words + 2 * ((words + 1) & ~1ll) + 4 * hv;
+}
+
 // ------------------------------------------------------------ batches
-// The non-empty streams of one batch of 32 lower neighbours, compacted.
+// The non-empty streams of a batch of 32 lower neighbours, compacted.
+// Each stream is cut into whole 32-id chunks and a remainder (< 32 ids).
 struct batch_smem {
-    int64_t start[32];   // first streamed position: twin(u,v) + 1
-    int32_t excl[32];    // offset of the stream in the batch's concatenation
-    int32_t u[32];       // the lower neighbour
-    uint32_t hits[32];   // triangles found on the stream
+    int64_t start[32];    // first streamed position: twin(u,v) + 1
+    int32_t len[32];      // stream length
+    int32_t cexcl[33];    // chunks before the stream; [nseg] = chunks in the batch
+    int32_t u[32];        // the lower neighbour
+    uint32_t hits[32];    // triangles found on the stream
+    int64_t rpos[32];     // streams with a remainder, compacted again: remainder start
+    int32_t rexcl[32];    // remainder ids before it
+    int32_t rseg[32];     // its stream
 };
 
-// Loads head entries [b, min(b+32, pe)); returns the concatenated length.
-__device__ __forceinline__ int load_batch(int lane, int64_t b, int64_t pe,
-                                          const int32_t* __restrict__ col,
-                                          const int64_t* __restrict__ twin,
-                                          const int32_t* __restrict__ hrem, batch_smem& bs,
-                                          int& nseg, int& my_excl) {
+struct batch_info {
+    int nseg, nchunks, nrem, nrseg;
+    int my_rexcl;         // remainder offset of remainder-stream `lane` (or INT_MAX)
+};
+
+// Loads head entries [b, min(b+32, pe)) into the warp's batch bookkeeping.
+__device__ __forceinline__ batch_info load_batch(int lane, int64_t b, int64_t pe,
+                                                 const int32_t* __restrict__ col,
+                                                 const int64_t* __restrict__ twin,
+                                                 const int32_t* __restrict__ hrem,
+                                                 batch_smem& bs) {
     const int64_t p = b + lane;
     int r = 0;
     if (p < pe) r = hrem[p];
-    int incl = r;
+    // one scan of (chunks << 16 | remainder): both sums fit 16 bits per
+    // batch because every stream is shorter than 2^16 (checked at build)
+    const unsigned packed = ((unsigned)(r >> 5) << 16) | (unsigned)(r & 31);
+    unsigned incl = packed;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        int x = __shfl_up_sync(FULL, incl, d);
+        const unsigned x = __shfl_up_sync(FULL, incl, d);
         if (lane >= d) incl += x;
     }
-    const int total = __shfl_sync(FULL, incl, 31);
+    const unsigned tot = __shfl_sync(FULL, incl, 31);
     const unsigned nz = __ballot_sync(FULL, r > 0);
+    const unsigned excl = incl - packed;
+    batch_info bi;
+    bi.nseg = __popc(nz);
+    bi.nchunks = (int)(tot >> 16);
+    bi.nrem = (int)(tot & 0xffffu);
     if (r > 0) {
         const int k = __popc(nz & ((1u << lane) - 1));
-        bs.start[k] = twin[p] + 1;
-        bs.excl[k] = incl - r;
+        const int64_t st = twin[p] + 1;
+        bs.start[k] = st;
+        bs.len[k] = r;
+        bs.cexcl[k] = (int)(excl >> 16);
         bs.u[k] = col[p];
         bs.hits[k] = 0;
     }
-    nseg = __popc(nz);
+    // second compaction: streams whose remainder is non-empty
+    const unsigned nzr = __ballot_sync(FULL, (r & 31) != 0);
+    if (r & 31) {
+        const int q = __popc(nzr & ((1u << lane) - 1));
+        const int k = __popc(nz & ((1u << lane) - 1));
+        bs.rpos[q] = twin[p] + 1 + (r & ~31);
+        bs.rexcl[q] = (int)(excl & 0xffffu);
+        bs.rseg[q] = k;
+    }
+    bi.nrseg = __popc(nzr);
+    if (lane == 0) bs.cexcl[bi.nseg] = bi.nchunks;
     __syncwarp();
-    my_excl = lane < nseg ? bs.excl[lane] : 0x7fffffff;
-    return total;
+    bi.my_rexcl = lane < bi.nrseg ? bs.rexcl[lane] : 0x7fffffff;
+    return bi;
 }
 
 // Credits the hits of each stream to △(u) and flags the edge (u, v).
@@ -166,60 +203,92 @@ __device__ __forceinline__ void close_batch(int lane, int nseg, batch_smem& bs,
     __syncwarp();
 }
 
-// Walks the concatenated streams of a batch and looks every id up in the
-// staged N_H(v).  CNT: per staged index counters in shared memory (else
-// the counts of w go straight to global memory).
 template <class LK, bool CNT>
-__device__ __forceinline__ void stream_batch(int lane, int total, int my_excl, const LK& lk,
+__device__ __forceinline__ bool on_id(const LK& lk, bool ok, int32_t w, int64_t pos, uint32_t* cnt,
+                                      int64_t h0, ull* __restrict__ tri, uint8_t* __restrict__ flag) {
+    int l = 0;
+    const bool hit = ok && lk.find(w, l);
+    if (hit) {
+        if (CNT) {
+            atomicAdd(&cnt[l], 1u);
+        } else {
+            atomicAdd(&tri[w], 1ull);
+            flag[h0 + l] = 1;
+        }
+        flag[pos] = 1;   // edge (u, w)
+    }
+    return hit;
+}
+
+// Looks every streamed id of a batch up in the staged N_H(v).
+// Phase 1: whole 32-id chunks, lane-consecutive, kIlp chunks in flight; the
+// stream of a chunk is one uniform search over the chunk prefix.
+// Phase 2: the remainders (< 32 ids per stream) as one concatenation walked
+// lane-consecutively; the stream of each lane comes from the mask of
+// remainder starts inside the window (one warp OR-reduction).
+template <class LK, bool CNT>
+__device__ __forceinline__ void stream_batch(int lane, const batch_info& bi, const LK& lk,
                                              batch_smem& bs, uint32_t* cnt, int64_t h0,
                                              const int32_t* __restrict__ col,
                                              ull* __restrict__ tri, uint8_t* __restrict__ flag) {
-    const unsigned le = FULL >> (31 - lane);           // lanes 0..lane
-    int s0 = -1;                                       // segment covering the id before the window
-    for (int F = 0; F < total; F += 32 * kIlp) {
+    for (int c0 = 0; c0 < bi.nchunks; c0 += kIlp) {
         int64_t pos[kIlp];
         int seg[kIlp];
-        unsigned smask[kIlp];
-        bool ok[kIlp];
         int32_t w[kIlp];
 #pragma unroll
         for (int k = 0; k < kIlp; ++k) {
+            const int c = c0 + k;
+            int s = 0;
+#pragma unroll
+            for (int step = 16; step; step >>= 1)
+                if (s + step < bi.nseg && bs.cexcl[s + step] <= c) s += step;
+            seg[k] = s;
+            pos[k] = bs.start[s] + ((int64_t)(c - bs.cexcl[s]) << 5) + lane;
+        }
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) w[k] = (c0 + k < bi.nchunks) ? __ldg(col + pos[k]) : -1;
+#pragma unroll
+        for (int k = 0; k < kIlp; ++k) {
+            const bool hit = on_id<LK, CNT>(lk, c0 + k < bi.nchunks, w[k], pos[k], cnt, h0, tri, flag);
+            const unsigned hm = __ballot_sync(FULL, hit);
+            if (lane == 0 && hm) atomicAdd(&bs.hits[seg[k]], (unsigned)__popc(hm));
+        }
+    }
+    if (bi.nrem == 0) return;
+    const unsigned le = FULL >> (31 - lane);           // lanes 0..lane
+    int s0 = -1;                                       // remainder stream before the window
+    for (int F = 0; F < bi.nrem; F += 32 * 2) {
+        int64_t pos[2];
+        int seg[2];
+        unsigned smask[2];
+        bool ok[2];
+        int32_t w[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
             const int Fk = F + 32 * k;
-            const int rel = my_excl - Fk;
-            const unsigned bit = (rel >= 0 && rel < 32) ? (1u << rel) : 0u;
-            smask[k] = __reduce_or_sync(FULL, bit);
+            const int rel = bi.my_rexcl - Fk;
+            smask[k] = __reduce_or_sync(FULL, (rel >= 0 && rel < 32) ? (1u << rel) : 0u);
             seg[k] = s0 + __popc(smask[k] & le);
             s0 += __popc(smask[k]);
             const int f = Fk + lane;
-            ok[k] = f < total;
-            pos[k] = ok[k] ? bs.start[seg[k]] + (f - bs.excl[seg[k]]) : 0;
+            ok[k] = f < bi.nrem;
+            pos[k] = ok[k] ? bs.rpos[seg[k]] + (f - bs.rexcl[seg[k]]) : 0;
         }
 #pragma unroll
-        for (int k = 0; k < kIlp; ++k) w[k] = ok[k] ? __ldg(col + pos[k]) : -1;
+        for (int k = 0; k < 2; ++k) w[k] = ok[k] ? __ldg(col + pos[k]) : -1;
 #pragma unroll
-        for (int k = 0; k < kIlp; ++k) {
-            int l = 0;
-            const bool hit = ok[k] && lk.find(w[k], l);
+        for (int k = 0; k < 2; ++k) {
+            const bool hit = on_id<LK, CNT>(lk, ok[k], w[k], pos[k], cnt, h0, tri, flag);
             const unsigned hm = __ballot_sync(FULL, hit);
             if (hm == 0) continue;
-            if (hit) {
-                if (CNT) {
-                    atomicAdd(&cnt[l], 1u);
-                } else {
-                    atomicAdd(&tri[w[k]], 1ull);
-                    flag[h0 + l] = 1;
-                }
-                flag[pos[k]] = 1;
-            }
-            // one shared atomic per (segment, window): the first lane of each
-            // segment run adds the run's hits
+            // the first lane of each stream's run adds the run's hits
             const bool leader = lane == 0 || ((smask[k] >> lane) & 1u);
             if (leader) {
                 const unsigned above = smask[k] & ~le;
                 const int end = above ? __ffs(above) - 1 : 32;
                 const unsigned range = (end == 32 ? FULL : ((1u << end) - 1)) & ~((1u << lane) - 1);
                 const unsigned c = __popc(hm & range);
-                if (c) atomicAdd(&bs.hits[seg[k]], c);
+                if (c) atomicAdd(&bs.hits[bs.rseg[seg[k]]], c);
             }
         }
     }
@@ -231,11 +300,11 @@ __device__ __forceinline__ void stream_batch(int lane, int total, int my_excl, c
 // first, and a common id is counted when its A element is consumed while
 // the current B element equals it.
 __device__ __forceinline__ void merge_batch(int lane, int nseg, const int32_t* A, int na,
-                                            batch_smem& bs, uint32_t* cnt, int total,
+                                            batch_smem& bs, uint32_t* cnt,
                                             const int32_t* __restrict__ col,
                                             uint8_t* __restrict__ flag) {
     for (int s = 0; s < nseg; ++s) {
-        const int nb = (s + 1 < nseg ? bs.excl[s + 1] : total) - bs.excl[s];
+        const int nb = bs.len[s];
         const int32_t* B = col + bs.start[s];
         const int L = na + nb;
         const int d0 = (int)(((int64_t)L * lane) >> 5), d1 = (int)(((int64_t)L * (lane + 1)) >> 5);
@@ -269,15 +338,66 @@ __device__ __forceinline__ ull warp_sum(ull x) {
     return x;
 }
 
+// Builds a bitmap staging with threads t of nt; barrier() separates phases.
+template <class Barrier>
+__device__ __forceinline__ lookup_bitmap build_bitmap(int t, int nt, uint8_t* region, int32_t v,
+                                                      int64_t h0, int hv, int32_t nbits,
+                                                      const int32_t* __restrict__ col,
+                                                      uint32_t*& cnt, Barrier barrier,
+                                                      uint32_t* scan_tmp, int lane, int warp, int nwarps) {
+    const int words = (nbits + 31) >> 5;
+    uint32_t* bits = (uint32_t*)region;
+    uint16_t* rank = (uint16_t*)(bits + words);
+    cnt = (uint32_t*)(rank + ((words + 1) & ~1));
+    const int32_t base = v + 1;
+    for (int i = t; i < words; i += nt) bits[i] = 0;
+    for (int i = t; i < hv; i += nt) cnt[i] = 0;
+    barrier();
+    for (int i = t; i < hv; i += nt) {
+        const int32_t off = col[h0 + i] - base;
+        atomicOr(&bits[off >> 5], 1u << (off & 31));
+    }
+    barrier();
+    // rank: per-thread contiguous slices, a warp scan of the slice sums and,
+    // for more than one warp, a scan over the warp totals
+    const int per = (words + nt - 1) / nt;
+    const int w0 = min(t * per, words), w1 = min(w0 + per, words);
+    uint32_t sum = 0;
+    for (int i = w0; i < w1; ++i) sum += __popc(bits[i]);
+    uint32_t incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t x = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += x;
+    }
+    uint32_t before = 0;
+    if (nwarps > 1) {
+        if (lane == 31) scan_tmp[warp] = incl;
+        barrier();
+        for (int k = 0; k < warp; ++k) before += scan_tmp[k];
+    }
+    uint32_t run = before + incl - sum;
+    for (int i = w0; i < w1; ++i) {
+        rank[i] = (uint16_t)run;
+        run += __popc(bits[i]);
+    }
+    barrier();
+    return lookup_bitmap{bits, rank, base, nbits};
+}
+
 // ------------------------------------------------------------ warp items
-// One warp per item; N_H(v) (at most TC_WARP_CAP ids) staged as a sorted list.
+// One warp per item, N_H(v) staged in the warp's own shared region: a
+// bitmap when its window fits, else a sorted list (|N_H(v)| <= TC_WARP_CAP).
+constexpr int kWarpSmem = 8 * TC_WARP_CAP;
 struct warp_smem {
-    int32_t ids[TC_WARP_CAP];
-    uint32_t cnt[TC_WARP_CAP];
+    uint8_t region[kWarpSmem];
     batch_smem bs;
 };
+constexpr int kWarpItemsPerFetch = 2;
 
-constexpr int kWarpItemsPerFetch = 4;
+__device__ __forceinline__ bool warp_bitmap_fits(int64_t words, int64_t hv) {
+    return hv < 65536 && bitmap_bytes(words, hv) <= kWarpSmem;
+}
 
 template <bool MERGE>
 __global__ void __launch_bounds__(TC_CTA_THREADS)
@@ -285,12 +405,14 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
              const int64_t* __restrict__ hstart, const int64_t* __restrict__ twin,
              const int32_t* __restrict__ hrem, const int32_t* __restrict__ it_v,
              const int64_t* __restrict__ it_pb, const int64_t* __restrict__ it_pe,
-             int64_t n_items, ull* __restrict__ cursor, ull* __restrict__ tri,
+             int64_t n_items, ull* __restrict__ cursor, int strategy, ull* __restrict__ tri,
              uint8_t* __restrict__ flag, ull* __restrict__ total) {
-    __shared__ warp_smem sm[kCtaWarps];
+    __shared__ __align__(16) warp_smem sm[kCtaWarps];
     const int lane = threadIdx.x & 31;
     warp_smem& ws = sm[threadIdx.x >> 5];
+    const bool allow_bitmap = !MERGE && (strategy == TC_STRATEGY_AUTO || strategy == TC_STRATEGY_BITMAP);
     ull tv_all = 0;
+    auto wbar = [] { __syncwarp(); };
     for (;;) {
         int64_t base = 0;
         if (lane == 0) base = (int64_t)atomicAdd(cursor, (ull)kWarpItemsPerFetch);
@@ -300,29 +422,39 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
         for (int64_t it = base; it < lim; ++it) {
             const int32_t v = it_v[it];
             const int64_t pb = it_pb[it], pe = it_pe[it];
-            const int64_t h0 = hstart[v];
-            const int hv = (int)(row_ptr[v + 1] - h0);
-            for (int i = lane; i < hv; i += 32) {
-                ws.ids[i] = col[h0 + i];
-                ws.cnt[i] = 0;
+            const int64_t h0 = hstart[v], h1 = row_ptr[v + 1];
+            const int hv = (int)(h1 - h0);
+            const int32_t nbits = col[h1 - 1] - v;
+            const bool use_bitmap = allow_bitmap && warp_bitmap_fits((nbits + 31) >> 5, hv);
+            uint32_t* cnt;
+            lookup_bitmap lb{};
+            int32_t* ids = (int32_t*)ws.region;
+            if (use_bitmap) {
+                lb = build_bitmap(lane, 32, ws.region, v, h0, hv, nbits, col, cnt, wbar, nullptr, lane, 0, 1);
+            } else {
+                cnt = (uint32_t*)(ids + TC_WARP_CAP);
+                for (int i = lane; i < hv; i += 32) {
+                    ids[i] = col[h0 + i];
+                    cnt[i] = 0;
+                }
+                __syncwarp();
             }
-            __syncwarp();
-            const lookup_sorted lk{ws.ids, hv};
+            const lookup_sorted ls{ids, hv};
             ull tv = 0;
             for (int64_t b = pb; b < pe; b += 32) {
-                int nseg, my_excl;
-                const int tot = load_batch(lane, b, pe, col, twin, hrem, ws.bs, nseg, my_excl);
-                if (tot > 0) {
-                    if (MERGE) merge_batch(lane, nseg, ws.ids, hv, ws.bs, ws.cnt, tot, col, flag);
-                    else stream_batch<lookup_sorted, true>(lane, tot, my_excl, lk, ws.bs, ws.cnt, h0, col, tri, flag);
+                const batch_info bi = load_batch(lane, b, pe, col, twin, hrem, ws.bs);
+                if (bi.nseg > 0) {
+                    if (MERGE) merge_batch(lane, bi.nseg, ids, hv, ws.bs, cnt, col, flag);
+                    else if (use_bitmap) stream_batch<lookup_bitmap, true>(lane, bi, lb, ws.bs, cnt, h0, col, tri, flag);
+                    else stream_batch<lookup_sorted, true>(lane, bi, ls, ws.bs, cnt, h0, col, tri, flag);
                 }
-                close_batch(lane, nseg, ws.bs, tri, flag, tv);
+                close_batch(lane, bi.nseg, ws.bs, tri, flag, tv);
             }
             __syncwarp();
             for (int i = lane; i < hv; i += 32) {
-                const uint32_t c = ws.cnt[i];
+                const uint32_t c = cnt[i];
                 if (c) {
-                    atomicAdd(&tri[ws.ids[i]], (ull)c);
+                    atomicAdd(&tri[col[h0 + i]], (ull)c);
                     flag[h0 + i] = 1;
                 }
             }
@@ -336,26 +468,31 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
 }
 
 // ------------------------------------------------------------- CTA items
-// One CTA per item; the 8 warps share the staged N_H(v) and take the
-// item's batches round-robin.
+// One CTA per item; the 8 warps share the staged N_H(v) and pull the
+// item's batches from a shared counter.
 template <int LOOK, bool MERGE>
 __global__ void __launch_bounds__(TC_CTA_THREADS)
 k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
             const int64_t* __restrict__ hstart, const int64_t* __restrict__ twin,
             const int32_t* __restrict__ hrem, const int32_t* __restrict__ it_v,
             const int64_t* __restrict__ it_pb, const int64_t* __restrict__ it_pe,
-            int64_t n_items, ull* __restrict__ cursor, ull* __restrict__ tri,
+            int64_t n_items, ull* __restrict__ cursor, int strategy, ull* __restrict__ tri,
             uint8_t* __restrict__ flag, ull* __restrict__ total) {
     extern __shared__ __align__(16) uint8_t dyn[];
     __shared__ batch_smem bsm[kCtaWarps];
     __shared__ int64_t s_item;
+    __shared__ int s_next;
     __shared__ ull s_tv[kCtaWarps];
     __shared__ uint32_t s_scan[kCtaWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nt = TC_CTA_THREADS;
+    const int t = threadIdx.x, nt = TC_CTA_THREADS;
+    auto cbar = [] { __syncthreads(); };
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(cursor, 1ull);
+        if (t == 0) {
+            s_item = (int64_t)atomicAdd(cursor, 1ull);
+            s_next = 0;
+        }
         __syncthreads();
         const int64_t it = s_item;
         if (it >= n_items) break;
@@ -368,48 +505,11 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         lookup_sorted ls{};
         lookup_global lg{};
         if (LOOK == L_BITMAP) {
-            // ids of N_H(v) lie in [v+1, col[h1-1]]
-            const int32_t base = v + 1;
-            const int32_t nbits = col[h1 - 1] - v;
-            const int words = (nbits + 31) >> 5;
-            uint32_t* bits = (uint32_t*)dyn;
-            uint32_t* rnk = bits + words;
-            cnt = rnk + words;
-            for (int i = threadIdx.x; i < words; i += nt) bits[i] = 0;
-            for (int i = threadIdx.x; i < hv; i += nt) cnt[i] = 0;
-            __syncthreads();
-            for (int i = threadIdx.x; i < hv; i += nt) {
-                const int32_t off = col[h0 + i] - base;
-                atomicOr(&bits[off >> 5], 1u << (off & 31));
-            }
-            __syncthreads();
-            // rank[k] = set bits in words [0, k): per-thread slices, warp
-            // scan of the slice sums, then a scan over the 8 warp totals
-            const int per = (words + nt - 1) / nt;
-            const int w0 = min((int)threadIdx.x * per, words), w1 = min(w0 + per, words);
-            uint32_t sum = 0;
-            for (int i = w0; i < w1; ++i) sum += __popc(bits[i]);
-            uint32_t incl = sum;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t x = __shfl_up_sync(FULL, incl, d);
-                if (lane >= d) incl += x;
-            }
-            if (lane == 31) s_scan[warp] = incl;
-            __syncthreads();
-            uint32_t before = 0;
-            for (int k = 0; k < warp; ++k) before += s_scan[k];
-            uint32_t run = before + incl - sum;
-            for (int i = w0; i < w1; ++i) {
-                rnk[i] = run;
-                run += __popc(bits[i]);
-            }
-            __syncthreads();
-            lb = lookup_bitmap{bits, rnk, base, nbits};
+            lb = build_bitmap(t, nt, dyn, v, h0, hv, col[h1 - 1] - v, col, cnt, cbar, s_scan, lane, warp, kCtaWarps);
         } else if (LOOK == L_SORTED) {
             int32_t* ids = (int32_t*)dyn;
             cnt = (uint32_t*)(ids + hv);
-            for (int i = threadIdx.x; i < hv; i += nt) {
+            for (int i = t; i < hv; i += nt) {
                 ids[i] = col[h0 + i];
                 cnt[i] = 0;
             }
@@ -420,26 +520,30 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         }
         ull tv = 0;
         batch_smem& bs = bsm[warp];
-        for (int64_t b = pb + 32 * warp; b < pe; b += 32 * kCtaWarps) {
-            int nseg, my_excl;
-            const int tot = load_batch(lane, b, pe, col, twin, hrem, bs, nseg, my_excl);
-            if (tot > 0) {
+        const int64_t nb = (pe - pb + 31) >> 5;
+        for (;;) {
+            int bidx = 0;
+            if (lane == 0) bidx = atomicAdd(&s_next, 1);
+            bidx = __shfl_sync(FULL, bidx, 0);
+            if (bidx >= nb) break;
+            const batch_info bi = load_batch(lane, pb + 32 * (int64_t)bidx, pe, col, twin, hrem, bs);
+            if (bi.nseg > 0) {
                 if (LOOK == L_BITMAP)
-                    stream_batch<lookup_bitmap, true>(lane, tot, my_excl, lb, bs, cnt, h0, col, tri, flag);
+                    stream_batch<lookup_bitmap, true>(lane, bi, lb, bs, cnt, h0, col, tri, flag);
                 else if (LOOK == L_SORTED && MERGE)
-                    merge_batch(lane, nseg, ls.ids, hv, bs, cnt, tot, col, flag);
+                    merge_batch(lane, bi.nseg, ls.ids, hv, bs, cnt, col, flag);
                 else if (LOOK == L_SORTED)
-                    stream_batch<lookup_sorted, true>(lane, tot, my_excl, ls, bs, cnt, h0, col, tri, flag);
+                    stream_batch<lookup_sorted, true>(lane, bi, ls, bs, cnt, h0, col, tri, flag);
                 else
-                    stream_batch<lookup_global, false>(lane, tot, my_excl, lg, bs, nullptr, h0, col, tri, flag);
+                    stream_batch<lookup_global, false>(lane, bi, lg, bs, nullptr, h0, col, tri, flag);
             }
-            close_batch(lane, nseg, bs, tri, flag, tv);
+            close_batch(lane, bi.nseg, bs, tri, flag, tv);
         }
         tv = warp_sum(tv);
         if (lane == 0) s_tv[warp] = tv;
         __syncthreads();
         if (LOOK != L_GLOBAL) {
-            for (int i = threadIdx.x; i < hv; i += nt) {
+            for (int i = t; i < hv; i += nt) {
                 const uint32_t c = cnt[i];
                 if (c) {
                     atomicAdd(&tri[col[h0 + i]], (ull)c);
@@ -447,12 +551,12 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
                 }
             }
         }
-        if (threadIdx.x == 0) {
-            ull t = 0;
-            for (int k = 0; k < kCtaWarps; ++k) t += s_tv[k];
-            if (t) {
-                atomicAdd(&tri[v], t);
-                atomicAdd(total, t);
+        if (t == 0) {
+            ull sum = 0;
+            for (int k = 0; k < kCtaWarps; ++k) sum += s_tv[k];
+            if (sum) {
+                atomicAdd(&tri[v], sum);
+                atomicAdd(total, sum);
             }
         }
     }
@@ -482,16 +586,28 @@ __global__ void k_classify(const int64_t* __restrict__ row_ptr, const int64_t* _
         if (W > 0 && hv > 0) {
             const int64_t nbits = (int64_t)col[e - 1] - r;
             const int64_t words = (nbits + 31) >> 5;
-            const int64_t bm_bytes = 8 * words + 4 * hv;
-            const bool fit_s = bm_bytes <= kBitmapSmallSmem;
-            const bool fit_l = bm_bytes <= kBitmapLargeSmem;
-            const bool bitmap_ok = strategy == TC_STRATEGY_BITMAP ||
-                                   (strategy == TC_STRATEGY_AUTO && W >= kCtaMinWork && W >= 2 * words);
-            if (strategy == TC_STRATEGY_GLOBAL) c = TC_CLS_CTA_LIST;
-            else if (bitmap_ok && fit_s) c = TC_CLS_BITMAP_S;
-            else if (bitmap_ok && fit_l) c = TC_CLS_BITMAP_L;
-            else if (hv <= TC_WARP_CAP) c = TC_CLS_WARP;
-            else c = TC_CLS_CTA_LIST;
+            const int64_t bm = hv < 65536 ? bitmap_bytes(words, hv) : (int64_t)1 << 62;
+            const bool warp_bm = bm <= kWarpSmem;
+            const bool warp_list = hv <= TC_WARP_CAP;
+            const bool cta_s = bm <= kBitmapSmallSmem, cta_l = bm <= kBitmapLargeSmem;
+            if (strategy == TC_STRATEGY_GLOBAL) {
+                c = TC_CLS_CTA_LIST;
+            } else if (strategy == TC_STRATEGY_BSEARCH || strategy == TC_STRATEGY_MERGE) {
+                c = warp_list ? TC_CLS_WARP : TC_CLS_CTA_LIST;
+            } else if (strategy == TC_STRATEGY_BITMAP) {
+                c = warp_bm ? TC_CLS_WARP : cta_s ? TC_CLS_BITMAP_S : cta_l ? TC_CLS_BITMAP_L
+                  : warp_list ? TC_CLS_WARP : TC_CLS_CTA_LIST;
+            } else {
+                // AUTO: heavy vertices on a CTA bitmap when zeroing it is cheap
+                // next to the work; the rest on a warp (bitmap or list)
+                const bool heavy = W >= kCtaMinWork && W >= 2 * words;
+                if (heavy && !warp_bm && cta_s) c = TC_CLS_BITMAP_S;
+                else if (heavy && !warp_bm && cta_l) c = TC_CLS_BITMAP_L;
+                else if (warp_bm || warp_list) c = TC_CLS_WARP;
+                else if (cta_s) c = TC_CLS_BITMAP_S;
+                else if (cta_l) c = TC_CLS_BITMAP_L;
+                else c = TC_CLS_CTA_LIST;
+            }
             const int64_t chunk = c == TC_CLS_WARP ? kWarpChunk : kCtaChunk;
             chunks = (W + chunk - 1) / chunk;
             if (chunks > lv) chunks = lv;
@@ -546,8 +662,8 @@ tc_status launch_persistent(K kernel, const char* name, size_t smem, int64_t ite
     int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, items);
     launch_scope ls(name, s);
     kernel<<<(int)blocks, TC_CTA_THREADS, smem, s>>>(g->row_ptr, g->col, g->hstart, g->twin, g->hrem,
-                                                     p.v[c], p.pb[c], p.pe[c], items, cursor, g->tri,
-                                                     g->flag, g->counters);
+                                                     p.v[c], p.pb[c], p.pe[c], items, cursor,
+                                                     g->strategy, g->tri, g->flag, g->counters);
     TC_LAUNCH_CHECK();
     return TC_OK;
 }
@@ -632,7 +748,7 @@ tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s) {
     p.smem[TC_CLS_BITMAP_S] = kBitmapSmallSmem;
     p.smem[TC_CLS_BITMAP_L] = kBitmapLargeSmem;
     p.smem[TC_CLS_WARP] = 0;
-    p.smem[TC_CLS_CTA_LIST] = kBitmapLargeSmem;
+    p.smem[TC_CLS_CTA_LIST] = kCtaListSmem;
     p.strategy = strategy;
     // algorithmic bytes of each class's kernel: stage N_H(v) once (4 hv),
     // read each head entry's label, twin and stream length (16), stream each
