@@ -220,18 +220,15 @@ __device__ __forceinline__ bool on_id(const LK& lk, bool ok, int32_t w, int64_t 
     return hit;
 }
 
-// Looks every streamed id of a batch up in the staged N_H(v).
-// Phase 1: whole 32-id chunks, lane-consecutive, kIlp chunks in flight; the
-// stream of a chunk is one uniform search over the chunk prefix.
-// Phase 2: the remainders (< 32 ids per stream) as one concatenation walked
-// lane-consecutively; the stream of each lane comes from the mask of
-// remainder starts inside the window (one warp OR-reduction).
+// Phase 1 of a batch: whole 32-id chunks [c_begin, c_end) of its streams,
+// lane-consecutive ids, kIlp chunks in flight; the stream of a chunk is
+// one uniform search over the chunk prefix.
 template <class LK, bool CNT>
-__device__ __forceinline__ void stream_batch(int lane, const batch_info& bi, const LK& lk,
-                                             batch_smem& bs, uint32_t* cnt, int64_t h0,
-                                             const int32_t* __restrict__ col,
-                                             ull* __restrict__ tri, uint8_t* __restrict__ flag) {
-    for (int c0 = 0; c0 < bi.nchunks; c0 += kIlp) {
+__device__ __forceinline__ void stream_chunks(int lane, int c_begin, int c_end, int nseg,
+                                              const LK& lk, batch_smem& bs, uint32_t* cnt,
+                                              int64_t h0, const int32_t* __restrict__ col,
+                                              ull* __restrict__ tri, uint8_t* __restrict__ flag) {
+    for (int c0 = c_begin; c0 < c_end; c0 += kIlp) {
         int64_t pos[kIlp];
         int seg[kIlp];
         int32_t w[kIlp];
@@ -241,19 +238,30 @@ __device__ __forceinline__ void stream_batch(int lane, const batch_info& bi, con
             int s = 0;
 #pragma unroll
             for (int step = 16; step; step >>= 1)
-                if (s + step < bi.nseg && bs.cexcl[s + step] <= c) s += step;
+                if (s + step < nseg && bs.cexcl[s + step] <= c) s += step;
             seg[k] = s;
             pos[k] = bs.start[s] + ((int64_t)(c - bs.cexcl[s]) << 5) + lane;
         }
 #pragma unroll
-        for (int k = 0; k < kIlp; ++k) w[k] = (c0 + k < bi.nchunks) ? __ldg(col + pos[k]) : -1;
+        for (int k = 0; k < kIlp; ++k) w[k] = (c0 + k < c_end) ? __ldg(col + pos[k]) : -1;
 #pragma unroll
         for (int k = 0; k < kIlp; ++k) {
-            const bool hit = on_id<LK, CNT>(lk, c0 + k < bi.nchunks, w[k], pos[k], cnt, h0, tri, flag);
+            const bool hit = on_id<LK, CNT>(lk, c0 + k < c_end, w[k], pos[k], cnt, h0, tri, flag);
             const unsigned hm = __ballot_sync(FULL, hit);
             if (lane == 0 && hm) atomicAdd(&bs.hits[seg[k]], (unsigned)__popc(hm));
         }
     }
+}
+
+// Phase 2 of a batch: the remainders (< 32 ids per stream) as one
+// concatenation walked lane-consecutively; the stream of each lane comes
+// from the mask of remainder starts inside the window (one warp
+// OR-reduction).
+template <class LK, bool CNT>
+__device__ __forceinline__ void stream_remainders(int lane, const batch_info& bi, const LK& lk,
+                                                  batch_smem& bs, uint32_t* cnt, int64_t h0,
+                                                  const int32_t* __restrict__ col,
+                                                  ull* __restrict__ tri, uint8_t* __restrict__ flag) {
     if (bi.nrem == 0) return;
     const unsigned le = FULL >> (31 - lane);           // lanes 0..lane
     int s0 = -1;                                       // remainder stream before the window
@@ -292,6 +300,16 @@ __device__ __forceinline__ void stream_batch(int lane, const batch_info& bi, con
             }
         }
     }
+}
+
+// Every streamed id of a batch, by one warp.
+template <class LK, bool CNT>
+__device__ __forceinline__ void stream_batch(int lane, const batch_info& bi, const LK& lk,
+                                             batch_smem& bs, uint32_t* cnt, int64_t h0,
+                                             const int32_t* __restrict__ col,
+                                             ull* __restrict__ tri, uint8_t* __restrict__ flag) {
+    stream_chunks<LK, CNT>(lane, 0, bi.nchunks, bi.nseg, lk, bs, cnt, h0, col, tri, flag);
+    stream_remainders<LK, CNT>(lane, bi, lk, bs, cnt, h0, col, tri, flag);
 }
 
 // Merge-path intersection of the staged A = N_H(v) (shared, ascending)
@@ -468,8 +486,40 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
 }
 
 // ------------------------------------------------------------- CTA items
-// One CTA per item; the 8 warps share the staged N_H(v) and pull the
-// item's batches from a shared counter.
+// One CTA per item; the 8 warps share the staged N_H(v).  The item's head
+// entries are taken in rounds of 256 (one batch per warp); inside a round
+// all warps pull groups of whole 32-id chunks from the round's combined
+// chunk space, so that a few long streams do not leave warps idle, and
+// each warp then walks its own batch's remainders.
+template <class LK, bool CNT>
+__device__ __forceinline__ void cta_round_chunks(int lane, int* s_next, const int* s_off,
+                                                 const int* s_nseg, batch_smem* bsm,
+                                                 const LK& lk, uint32_t* cnt, int64_t h0,
+                                                 const int32_t* __restrict__ col,
+                                                 ull* __restrict__ tri, uint8_t* __restrict__ flag) {
+    const int total = s_off[kCtaWarps];
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(s_next, 1);
+        g = __shfl_sync(FULL, g, 0);
+        const int c0 = g * kIlp;
+        if (c0 >= total) break;
+        // the group may straddle batches: split it at the owners' boundaries
+        int c = c0;
+        const int c_end = min(c0 + kIlp, total);
+        while (c < c_end) {
+            int w = 0;
+#pragma unroll
+            for (int step = 4; step; step >>= 1)
+                if (w + step < kCtaWarps && s_off[w + step] <= c) w += step;
+            const int stop = min(c_end, s_off[w + 1]);
+            stream_chunks<LK, CNT>(lane, c - s_off[w], stop - s_off[w], s_nseg[w], lk, bsm[w], cnt, h0,
+                                   col, tri, flag);
+            c = stop;
+        }
+    }
+}
+
 template <int LOOK, bool MERGE>
 __global__ void __launch_bounds__(TC_CTA_THREADS)
 k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -482,6 +532,8 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
     __shared__ batch_smem bsm[kCtaWarps];
     __shared__ int64_t s_item;
     __shared__ int s_next;
+    __shared__ int s_off[kCtaWarps + 1];
+    __shared__ int s_nseg[kCtaWarps];
     __shared__ ull s_tv[kCtaWarps];
     __shared__ uint32_t s_scan[kCtaWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -489,10 +541,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
     auto cbar = [] { __syncthreads(); };
     for (;;) {
         __syncthreads();
-        if (t == 0) {
-            s_item = (int64_t)atomicAdd(cursor, 1ull);
-            s_next = 0;
-        }
+        if (t == 0) s_item = (int64_t)atomicAdd(cursor, 1ull);
         __syncthreads();
         const int64_t it = s_item;
         if (it >= n_items) break;
@@ -520,24 +569,34 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         }
         ull tv = 0;
         batch_smem& bs = bsm[warp];
-        const int64_t nb = (pe - pb + 31) >> 5;
-        for (;;) {
-            int bidx = 0;
-            if (lane == 0) bidx = atomicAdd(&s_next, 1);
-            bidx = __shfl_sync(FULL, bidx, 0);
-            if (bidx >= nb) break;
-            const batch_info bi = load_batch(lane, pb + 32 * (int64_t)bidx, pe, col, twin, hrem, bs);
-            if (bi.nseg > 0) {
-                if (LOOK == L_BITMAP)
-                    stream_batch<lookup_bitmap, true>(lane, bi, lb, bs, cnt, h0, col, tri, flag);
-                else if (LOOK == L_SORTED && MERGE)
-                    merge_batch(lane, bi.nseg, ls.ids, hv, bs, cnt, col, flag);
-                else if (LOOK == L_SORTED)
-                    stream_batch<lookup_sorted, true>(lane, bi, ls, bs, cnt, h0, col, tri, flag);
-                else
-                    stream_batch<lookup_global, false>(lane, bi, lg, bs, nullptr, h0, col, tri, flag);
+        for (int64_t r0 = pb; r0 < pe; r0 += 32 * kCtaWarps) {
+            const batch_info bi = load_batch(lane, r0 + 32 * warp, pe, col, twin, hrem, bs);
+            if (lane == 0) {
+                s_nseg[warp] = bi.nseg;
+                s_off[warp + 1] = bi.nchunks;
             }
+            __syncthreads();
+            if (t == 0) {
+                s_off[0] = 0;
+                for (int k = 1; k <= kCtaWarps; ++k) s_off[k] += s_off[k - 1];
+                s_next = 0;
+            }
+            __syncthreads();
+            if (MERGE) {
+                if (bi.nseg > 0) merge_batch(lane, bi.nseg, ls.ids, hv, bs, cnt, col, flag);
+            } else if (LOOK == L_BITMAP) {
+                cta_round_chunks<lookup_bitmap, true>(lane, &s_next, s_off, s_nseg, bsm, lb, cnt, h0, col, tri, flag);
+                stream_remainders<lookup_bitmap, true>(lane, bi, lb, bs, cnt, h0, col, tri, flag);
+            } else if (LOOK == L_SORTED) {
+                cta_round_chunks<lookup_sorted, true>(lane, &s_next, s_off, s_nseg, bsm, ls, cnt, h0, col, tri, flag);
+                stream_remainders<lookup_sorted, true>(lane, bi, ls, bs, cnt, h0, col, tri, flag);
+            } else {
+                cta_round_chunks<lookup_global, false>(lane, &s_next, s_off, s_nseg, bsm, lg, nullptr, h0, col, tri, flag);
+                stream_remainders<lookup_global, false>(lane, bi, lg, bs, nullptr, h0, col, tri, flag);
+            }
+            __syncthreads();   // every warp's chunks of this round are done
             close_batch(lane, bi.nseg, bs, tri, flag, tv);
+            __syncthreads();   // before the batches are overwritten
         }
         tv = warp_sum(tv);
         if (lane == 0) s_tv[warp] = tv;
