@@ -33,6 +33,7 @@ WORKLOADS = {
     "rmat-s24-ef16": dict(kind="rmat", scale=24, edge_factor=16, seed=0x5EED0018),
     "rmat-s12-ef16": dict(kind="rmat", scale=12, edge_factor=16, seed=0x5EED0000),
     "rmat-s20-ef16": dict(kind="rmat", scale=20, edge_factor=16, seed=0x5EED0014),
+    "rmat-s21-ef16": dict(kind="rmat", scale=21, edge_factor=16, seed=0x5EED0015),
     "rmat-s22-ef16": dict(kind="rmat", scale=22, edge_factor=16, seed=0x5EED0016),
     "grid4096-diag05-cl21": dict(kind="grid", side=4096, pdiag=0.05, gamma=2.1, mean_deg=4.0,
                                  seed=0x5EED0002),

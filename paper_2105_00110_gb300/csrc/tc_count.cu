@@ -40,7 +40,7 @@ namespace {
 typedef unsigned long long ull;
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kIlp = 4;                 // 32-id windows in flight per lane
+constexpr int kIlp = 8;                 // 32-id chunks in flight per lane
 constexpr int kCtaWarps = TC_CTA_THREADS / 32;
 
 // Planner constants.
