@@ -40,11 +40,10 @@ namespace {
 typedef unsigned long long ull;
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kIlp = 8;                 // 32-id chunks in flight per lane
 constexpr int kCtaWarps = TC_CTA_THREADS / 32;
 
 // Planner constants.
-constexpr int64_t kBitmapSmallSmem = 34 * 1024;   // dynamic smem of the small-bitmap CTA kernel (5 CTAs per SM)
+constexpr int64_t kBitmapSmallSmem = 32 * 1024;   // dynamic smem of the small-bitmap CTA kernel (5 CTAs per SM)
 constexpr int64_t kBitmapLargeSmem = 100 * 1024;  // ... of the large-bitmap CTA kernel
 constexpr int64_t kCtaListSmem = 100 * 1024;      // ... of the CTA sorted-list kernel
 constexpr int64_t kCtaChunk = 65536;              // target wedges per CTA item
@@ -118,239 +117,6 @@ __host__ __device__ __forceinline__ int64_t bitmap_bytes(int64_t words, int64_t 
     return 4 * words + 2 * ((words + 1) & ~1ll) + 4 * hv;
 }
 
-// ------------------------------------------------------------ batches
-// The non-empty streams of a batch of 32 lower neighbours, compacted.
-// Each stream is cut into whole 32-id chunks and a remainder (< 32 ids).
-struct batch_smem {
-    int64_t start[32];    // first streamed position: twin(u,v) + 1
-    int32_t len[32];      // stream length
-    int32_t cexcl[33];    // chunks before the stream; [nseg] = chunks in the batch
-    int32_t u[32];        // the lower neighbour
-    uint32_t hits[32];    // triangles found on the stream
-    int64_t rpos[32];     // streams with a remainder, compacted again: remainder start
-    int32_t rexcl[32];    // remainder ids before it
-    int32_t rseg[32];     // its stream
-};
-
-struct batch_info {
-    int nseg, nchunks, nrem, nrseg;
-    int my_rexcl;         // remainder offset of remainder-stream `lane` (or INT_MAX)
-};
-
-// Loads head entries [b, min(b+32, pe)) into the warp's batch bookkeeping.
-__device__ __forceinline__ batch_info load_batch(int lane, int64_t b, int64_t pe,
-                                                 const int32_t* __restrict__ col,
-                                                 const int64_t* __restrict__ twin,
-                                                 const int32_t* __restrict__ hrem,
-                                                 batch_smem& bs) {
-    const int64_t p = b + lane;
-    int r = 0;
-    if (p < pe) r = hrem[p];
-    // one scan of (chunks << 16 | remainder): both sums fit 16 bits per
-    // batch because every stream is shorter than 2^16 (checked at build)
-    const unsigned packed = ((unsigned)(r >> 5) << 16) | (unsigned)(r & 31);
-    unsigned incl = packed;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned x = __shfl_up_sync(FULL, incl, d);
-        if (lane >= d) incl += x;
-    }
-    const unsigned tot = __shfl_sync(FULL, incl, 31);
-    const unsigned nz = __ballot_sync(FULL, r > 0);
-    const unsigned excl = incl - packed;
-    batch_info bi;
-    bi.nseg = __popc(nz);
-    bi.nchunks = (int)(tot >> 16);
-    bi.nrem = (int)(tot & 0xffffu);
-    if (r > 0) {
-        const int k = __popc(nz & ((1u << lane) - 1));
-        const int64_t st = twin[p] + 1;
-        bs.start[k] = st;
-        bs.len[k] = r;
-        bs.cexcl[k] = (int)(excl >> 16);
-        bs.u[k] = col[p];
-        bs.hits[k] = 0;
-    }
-    // second compaction: streams whose remainder is non-empty
-    const unsigned nzr = __ballot_sync(FULL, (r & 31) != 0);
-    if (r & 31) {
-        const int q = __popc(nzr & ((1u << lane) - 1));
-        const int k = __popc(nz & ((1u << lane) - 1));
-        bs.rpos[q] = twin[p] + 1 + (r & ~31);
-        bs.rexcl[q] = (int)(excl & 0xffffu);
-        bs.rseg[q] = k;
-    }
-    bi.nrseg = __popc(nzr);
-    if (lane == 0) bs.cexcl[bi.nseg] = bi.nchunks;
-    __syncwarp();
-    bi.my_rexcl = lane < bi.nrseg ? bs.rexcl[lane] : 0x7fffffff;
-    return bi;
-}
-
-// Credits the hits of each stream to △(u) and flags the edge (u, v).
-__device__ __forceinline__ void close_batch(int lane, int nseg, batch_smem& bs,
-                                            ull* __restrict__ tri, uint8_t* __restrict__ flag,
-                                            ull& tv) {
-    __syncwarp();
-    if (lane < nseg) {
-        const uint32_t c = bs.hits[lane];
-        if (c) {
-            atomicAdd(&tri[bs.u[lane]], (ull)c);
-            flag[bs.start[lane] - 1] = 1;   // twin(u, v): the canonical entry of (u, v)
-            tv += c;
-        }
-    }
-    __syncwarp();
-}
-
-template <class LK, bool CNT>
-__device__ __forceinline__ bool on_id(const LK& lk, bool ok, int32_t w, int64_t pos, uint32_t* cnt,
-                                      int64_t h0, ull* __restrict__ tri, uint8_t* __restrict__ flag) {
-    int l = 0;
-    const bool hit = ok && lk.find(w, l);
-    if (hit) {
-        if (CNT) {
-            atomicAdd(&cnt[l], 1u);
-        } else {
-            atomicAdd(&tri[w], 1ull);
-            flag[h0 + l] = 1;
-        }
-        flag[pos] = 1;   // edge (u, w)
-    }
-    return hit;
-}
-
-// Phase 1 of a batch: whole 32-id chunks [c_begin, c_end) of its streams,
-// lane-consecutive ids, kIlp chunks in flight; the stream of a chunk is
-// one uniform search over the chunk prefix.
-template <class LK, bool CNT>
-__device__ __forceinline__ void stream_chunks(int lane, int c_begin, int c_end, int nseg,
-                                              const LK& lk, batch_smem& bs, uint32_t* cnt,
-                                              int64_t h0, const int32_t* __restrict__ col,
-                                              ull* __restrict__ tri, uint8_t* __restrict__ flag) {
-    for (int c0 = c_begin; c0 < c_end; c0 += kIlp) {
-        int64_t pos[kIlp];
-        int seg[kIlp];
-        int32_t w[kIlp];
-#pragma unroll
-        for (int k = 0; k < kIlp; ++k) {
-            const int c = c0 + k;
-            int s = 0;
-#pragma unroll
-            for (int step = 16; step; step >>= 1)
-                if (s + step < nseg && bs.cexcl[s + step] <= c) s += step;
-            seg[k] = s;
-            pos[k] = bs.start[s] + ((int64_t)(c - bs.cexcl[s]) << 5) + lane;
-        }
-#pragma unroll
-        for (int k = 0; k < kIlp; ++k) w[k] = (c0 + k < c_end) ? __ldg(col + pos[k]) : -1;
-#pragma unroll
-        for (int k = 0; k < kIlp; ++k) {
-            const bool hit = on_id<LK, CNT>(lk, c0 + k < c_end, w[k], pos[k], cnt, h0, tri, flag);
-            const unsigned hm = __ballot_sync(FULL, hit);
-            if (lane == 0 && hm) atomicAdd(&bs.hits[seg[k]], (unsigned)__popc(hm));
-        }
-    }
-}
-
-// Phase 2 of a batch: the remainders (< 32 ids per stream) as one
-// concatenation walked lane-consecutively; the stream of each lane comes
-// from the mask of remainder starts inside the window (one warp
-// OR-reduction).
-template <class LK, bool CNT>
-__device__ __forceinline__ void stream_remainders(int lane, const batch_info& bi, const LK& lk,
-                                                  batch_smem& bs, uint32_t* cnt, int64_t h0,
-                                                  const int32_t* __restrict__ col,
-                                                  ull* __restrict__ tri, uint8_t* __restrict__ flag) {
-    if (bi.nrem == 0) return;
-    const unsigned le = FULL >> (31 - lane);           // lanes 0..lane
-    int s0 = -1;                                       // remainder stream before the window
-    for (int F = 0; F < bi.nrem; F += 32 * 2) {
-        int64_t pos[2];
-        int seg[2];
-        unsigned smask[2];
-        bool ok[2];
-        int32_t w[2];
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int Fk = F + 32 * k;
-            const int rel = bi.my_rexcl - Fk;
-            smask[k] = __reduce_or_sync(FULL, (rel >= 0 && rel < 32) ? (1u << rel) : 0u);
-            seg[k] = s0 + __popc(smask[k] & le);
-            s0 += __popc(smask[k]);
-            const int f = Fk + lane;
-            ok[k] = f < bi.nrem;
-            pos[k] = ok[k] ? bs.rpos[seg[k]] + (f - bs.rexcl[seg[k]]) : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) w[k] = ok[k] ? __ldg(col + pos[k]) : -1;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const bool hit = on_id<LK, CNT>(lk, ok[k], w[k], pos[k], cnt, h0, tri, flag);
-            const unsigned hm = __ballot_sync(FULL, hit);
-            if (hm == 0) continue;
-            // the first lane of each stream's run adds the run's hits
-            const bool leader = lane == 0 || ((smask[k] >> lane) & 1u);
-            if (leader) {
-                const unsigned above = smask[k] & ~le;
-                const int end = above ? __ffs(above) - 1 : 32;
-                const unsigned range = (end == 32 ? FULL : ((1u << end) - 1)) & ~((1u << lane) - 1);
-                const unsigned c = __popc(hm & range);
-                if (c) atomicAdd(&bs.hits[bs.rseg[seg[k]]], c);
-            }
-        }
-    }
-}
-
-// Every streamed id of a batch, by one warp.
-template <class LK, bool CNT>
-__device__ __forceinline__ void stream_batch(int lane, const batch_info& bi, const LK& lk,
-                                             batch_smem& bs, uint32_t* cnt, int64_t h0,
-                                             const int32_t* __restrict__ col,
-                                             ull* __restrict__ tri, uint8_t* __restrict__ flag) {
-    stream_chunks<LK, CNT>(lane, 0, bi.nchunks, bi.nseg, lk, bs, cnt, h0, col, tri, flag);
-    stream_remainders<LK, CNT>(lane, bi, lk, bs, cnt, h0, col, tri, flag);
-}
-
-// Merge-path intersection of the staged A = N_H(v) (shared, ascending)
-// with each stream B of the batch in turn.  The 32 lanes split the merge
-// path of A and B into equal diagonals; on ties the A element is consumed
-// first, and a common id is counted when its A element is consumed while
-// the current B element equals it.
-__device__ __forceinline__ void merge_batch(int lane, int nseg, const int32_t* A, int na,
-                                            batch_smem& bs, uint32_t* cnt,
-                                            const int32_t* __restrict__ col,
-                                            uint8_t* __restrict__ flag) {
-    for (int s = 0; s < nseg; ++s) {
-        const int nb = bs.len[s];
-        const int32_t* B = col + bs.start[s];
-        const int L = na + nb;
-        const int d0 = (int)(((int64_t)L * lane) >> 5), d1 = (int)(((int64_t)L * (lane + 1)) >> 5);
-        int lo = max(0, d0 - nb), hi = min(d0, na);
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (A[mid] <= __ldg(B + (d0 - mid - 1))) lo = mid + 1; else hi = mid;
-        }
-        int i = lo, j = d0 - lo;
-        uint32_t found = 0;
-        for (int d = d0; d < d1; ++d) {
-            if (i < na && (j >= nb || A[i] <= __ldg(B + j))) {
-                if (j < nb && __ldg(B + j) == A[i]) {
-                    atomicAdd(&cnt[i], 1u);
-                    flag[bs.start[s] + j] = 1;
-                    ++found;
-                }
-                ++i;
-            } else {
-                ++j;
-            }
-        }
-        for (int o = 16; o; o >>= 1) found += __shfl_xor_sync(FULL, found, o);
-        if (lane == 0 && found) bs.hits[s] += found;
-        __syncwarp();
-    }
-}
-
 __device__ __forceinline__ ull warp_sum(ull x) {
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
     return x;
@@ -403,13 +169,266 @@ __device__ __forceinline__ lookup_bitmap build_bitmap(int t, int nt, uint8_t* re
     return lookup_bitmap{bits, rank, base, nbits};
 }
 
+// ------------------------------------------------------------ streams
+// A batch of head entries (lower neighbours u of the item's middle vertex v)
+// is a table of streams: stream i is col[p0, p0 + len), the part of N_H(u)
+// above v.  Its 4-aligned interior [va, vb) is read with 16-byte vector
+// loads (4 ids per lane); the at most 6 ids outside it (head and tail) are
+// read one by one by the lane that owns the stream.
+template <int N>
+struct stream_table {
+    int64_t p0[N];
+    int64_t va[N];
+    int64_t vb[N];
+    int32_t len[N];
+    int32_t u[N];
+    uint32_t hits[N];
+    int32_t pre[N + 1];   // prefix of vector work (CTA: 128-id chunks; warp: 4-id units, compacted)
+    int32_t sidx[N];      // warp tables: compacted stream of each unit run
+};
+
+// Lane `lane` loads head entry p (if p < pe) into slot i of the table.
+template <int N>
+__device__ __forceinline__ void load_entry(int64_t p, int64_t pe, int i,
+                                           const int32_t* __restrict__ col,
+                                           const int64_t* __restrict__ twin,
+                                           const int32_t* __restrict__ hrem, stream_table<N>& tb,
+                                           int64_t& va, int64_t& vb) {
+    int r = 0;
+    int64_t p0 = 0;
+    int32_t u = 0;
+    if (p < pe) {
+        r = hrem[p];
+        if (r > 0) {
+            p0 = twin[p] + 1;
+            u = col[p];
+        }
+    }
+    va = (p0 + 3) & ~3ll;
+    vb = (p0 + r) & ~3ll;
+    if (r == 0 || va >= vb) va = vb = 0;
+    tb.p0[i] = p0;
+    tb.va[i] = va;
+    tb.vb[i] = vb;
+    tb.len[i] = r;
+    tb.u[i] = u;
+    tb.hits[i] = 0;
+}
+
+// One streamed id at position pos: look it up; on a hit count the
+// triangle (u, v, w) at the staged index and flag the edge (u, w).
+template <class LK, bool CNT>
+__device__ __forceinline__ uint32_t visit(const LK& lk, int32_t w, int64_t pos, uint32_t* cnt, int64_t h0,
+                                          ull* __restrict__ tri, uint8_t* __restrict__ flag) {
+    int l = 0;
+    if (!lk.find(w, l)) return 0;
+    if (CNT) {
+        atomicAdd(&cnt[l], 1u);
+    } else {
+        atomicAdd(&tri[w], 1ull);
+        flag[h0 + l] = 1;
+    }
+    flag[pos] = 1;
+    return 1;
+}
+
+template <class LK, bool CNT>
+__device__ __forceinline__ uint32_t visit4(const LK& lk, int4 w, int64_t pos, uint32_t* cnt, int64_t h0,
+                                           ull* __restrict__ tri, uint8_t* __restrict__ flag) {
+    return visit<LK, CNT>(lk, w.x, pos, cnt, h0, tri, flag) + visit<LK, CNT>(lk, w.y, pos + 1, cnt, h0, tri, flag) +
+           visit<LK, CNT>(lk, w.z, pos + 2, cnt, h0, tri, flag) + visit<LK, CNT>(lk, w.w, pos + 3, cnt, h0, tri, flag);
+}
+
+__device__ __forceinline__ int4 load4(const int32_t* __restrict__ col, int64_t pos) {
+    return __ldg(reinterpret_cast<const int4*>(col + pos));
+}
+
+// The head and tail ids of stream i (outside its vector span), by one lane.
+template <class LK, bool CNT, int N>
+__device__ __forceinline__ void stream_scalars(int i, stream_table<N>& tb, const LK& lk, uint32_t* cnt,
+                                               int64_t h0, const int32_t* __restrict__ col,
+                                               ull* __restrict__ tri, uint8_t* __restrict__ flag) {
+    const int r = tb.len[i];
+    if (r == 0) return;
+    const int64_t p0 = tb.p0[i], va = tb.va[i], vb = tb.vb[i], pend = p0 + r;
+    const int64_t end1 = va < vb ? va : pend;
+    uint32_t h = 0;
+    for (int64_t e = p0; e < end1; ++e) h += visit<LK, CNT>(lk, __ldg(col + e), e, cnt, h0, tri, flag);
+    if (va < vb)
+        for (int64_t e = vb; e < pend; ++e) h += visit<LK, CNT>(lk, __ldg(col + e), e, cnt, h0, tri, flag);
+    if (h) atomicAdd(&tb.hits[i], h);
+}
+
+// Credits the hits of stream i to △(u) and flags the edge (u, v).
+template <int N>
+__device__ __forceinline__ void close_stream(int i, stream_table<N>& tb, ull* __restrict__ tri,
+                                             uint8_t* __restrict__ flag, ull& tv) {
+    const uint32_t c = tb.hits[i];
+    if (c) {
+        atomicAdd(&tri[tb.u[i]], (ull)c);
+        flag[tb.p0[i] - 1] = 1;   // twin(u, v): the canonical entry of (u, v)
+        tv += c;
+    }
+}
+
+constexpr int kVec = 4;   // 16-byte loads in flight per lane
+
+// Vector spans of a warp's 32 streams as one concatenation of 4-id units,
+// walked lane-consecutively (full lanes even on short streams).  The
+// stream of each lane comes from the mask of stream starts inside the
+// current 32-unit window (one warp OR-reduction).
+template <class LK, bool CNT>
+__device__ __forceinline__ void stream_units(int lane, stream_table<32>& tb, int64_t va, int64_t vb,
+                                             const LK& lk, uint32_t* cnt, int64_t h0,
+                                             const int32_t* __restrict__ col, ull* __restrict__ tri,
+                                             uint8_t* __restrict__ flag) {
+    const int nu = (int)((vb - va) >> 2);
+    const unsigned nz = __ballot_sync(FULL, nu > 0);
+    int incl = nu;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int x = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += x;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    if (total == 0) return;
+    if (nu > 0) {
+        const int k = __popc(nz & ((1u << lane) - 1));
+        tb.pre[k] = incl - nu;
+        tb.sidx[k] = lane;
+    }
+    __syncwarp();
+    const int nrun = __popc(nz);
+    const int my_excl = lane < nrun ? tb.pre[lane] : 0x7fffffff;
+    const unsigned le = FULL >> (31 - lane);
+    int s0 = -1;
+    for (int F = 0; F < total; F += 32 * kVec) {
+        int64_t pos[kVec];
+        int seg[kVec];
+        unsigned smask[kVec];
+        bool ok[kVec];
+        int4 w[kVec];
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+            const int Fj = F + 32 * j;
+            const int rel = my_excl - Fj;
+            smask[j] = __reduce_or_sync(FULL, (rel >= 0 && rel < 32) ? (1u << rel) : 0u);
+            seg[j] = s0 + __popc(smask[j] & le);
+            s0 += __popc(smask[j]);
+            const int q = Fj + lane;
+            ok[j] = q < total;
+            pos[j] = ok[j] ? tb.va[tb.sidx[seg[j]]] + 4ll * (q - tb.pre[seg[j]]) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) w[j] = ok[j] ? load4(col, pos[j]) : make_int4(-1, -1, -1, -1);
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+            const uint32_t h = ok[j] ? visit4<LK, CNT>(lk, w[j], pos[j], cnt, h0, tri, flag) : 0u;
+            if ((smask[j] & ~1u) == 0) {
+                // the whole window lies in one stream
+                const uint32_t sum = __reduce_add_sync(FULL, h);
+                if (lane == 0 && sum) atomicAdd(&tb.hits[tb.sidx[seg[j]]], sum);
+            } else if (h) {
+                atomicAdd(&tb.hits[tb.sidx[seg[j]]], h);
+            }
+        }
+    }
+}
+
+// Vector work of a CTA round: the round's 256 streams cut into 128-id
+// chunks (32 lanes x 4 ids, the last chunk of a stream partial); warp w
+// takes the contiguous chunk range [T w / 8, T (w+1) / 8) and walks it
+// stream by stream.
+template <class LK, bool CNT>
+__device__ __forceinline__ void stream_chunks(int lane, int warp, stream_table<256>& tb, const LK& lk,
+                                              uint32_t* cnt, int64_t h0, const int32_t* __restrict__ col,
+                                              ull* __restrict__ tri, uint8_t* __restrict__ flag) {
+    const int T = tb.pre[256];
+    const int cb = (int)(((int64_t)T * warp) >> 3), ce = (int)(((int64_t)T * (warp + 1)) >> 3);
+    if (cb >= ce) return;
+    int s = 0;   // last stream whose first chunk is at or before cb
+#pragma unroll
+    for (int step = 128; step; step >>= 1)
+        if (tb.pre[s + step] <= cb) s += step;
+    int k = cb - tb.pre[s];
+    for (int c = cb; c < ce; c += kVec) {
+        int64_t pos[kVec], lim[kVec];
+        int si[kVec];
+        int4 w[kVec];
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+            si[j] = s;
+            pos[j] = tb.va[s] + 128ll * k + 4 * lane;
+            lim[j] = (c + j < ce) ? tb.vb[s] : 0;
+            // advance to the next chunk (uniform across the warp)
+            if (c + j + 1 < ce) {
+                ++k;
+                while (k >= tb.pre[s + 1] - tb.pre[s]) {
+                    k = 0;
+                    ++s;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) w[j] = pos[j] < lim[j] ? load4(col, pos[j]) : make_int4(-1, -1, -1, -1);
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+            const uint32_t h = pos[j] < lim[j] ? visit4<LK, CNT>(lk, w[j], pos[j], cnt, h0, tri, flag) : 0u;
+            const uint32_t sum = __reduce_add_sync(FULL, h);
+            if (lane == 0 && sum) atomicAdd(&tb.hits[si[j]], sum);
+        }
+    }
+}
+
+// Merge-path intersection of the staged A = N_H(v) (shared, ascending)
+// with each stream B in turn.  The 32 lanes split the merge path of A and
+// B into equal diagonals; on ties the A element is consumed first, and a
+// common id is counted when its A element is consumed while the current B
+// element equals it.
+template <int N>
+__device__ __forceinline__ void merge_streams(int lane, int i0, int i1, stream_table<N>& tb,
+                                              const int32_t* A, int na, uint32_t* cnt,
+                                              const int32_t* __restrict__ col,
+                                              uint8_t* __restrict__ flag) {
+    for (int i = i0; i < i1; ++i) {
+        const int nb = tb.len[i];
+        if (nb == 0) continue;
+        const int64_t p0 = tb.p0[i];
+        const int32_t* B = col + p0;
+        const int L = na + nb;
+        const int d0 = (int)(((int64_t)L * lane) >> 5), d1 = (int)(((int64_t)L * (lane + 1)) >> 5);
+        int lo = max(0, d0 - nb), hi = min(d0, na);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (A[mid] <= __ldg(B + (d0 - mid - 1))) lo = mid + 1; else hi = mid;
+        }
+        int ia = lo, jb = d0 - lo;
+        uint32_t found = 0;
+        for (int d = d0; d < d1; ++d) {
+            if (ia < na && (jb >= nb || A[ia] <= __ldg(B + jb))) {
+                if (jb < nb && __ldg(B + jb) == A[ia]) {
+                    atomicAdd(&cnt[ia], 1u);
+                    flag[p0 + jb] = 1;
+                    ++found;
+                }
+                ++ia;
+            } else {
+                ++jb;
+            }
+        }
+        found = __reduce_add_sync(FULL, found);
+        if (lane == 0 && found) tb.hits[i] += found;
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------ warp items
 // One warp per item, N_H(v) staged in the warp's own shared region: a
 // bitmap when its window fits, else a sorted list (|N_H(v)| <= TC_WARP_CAP).
 constexpr int kWarpSmem = 8 * TC_WARP_CAP;
 struct warp_smem {
     uint8_t region[kWarpSmem];
-    batch_smem bs;
+    stream_table<32> tb;
 };
 constexpr int kWarpItemsPerFetch = 2;
 
@@ -460,15 +479,22 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
             const lookup_sorted ls{ids, hv};
             ull tv = 0;
             for (int64_t b = pb; b < pe; b += 32) {
-                const batch_info bi = load_batch(lane, b, pe, col, twin, hrem, ws.bs);
-                if (bi.nseg > 0) {
-                    if (MERGE) merge_batch(lane, bi.nseg, ids, hv, ws.bs, cnt, col, flag);
-                    else if (use_bitmap) stream_batch<lookup_bitmap, true>(lane, bi, lb, ws.bs, cnt, h0, col, tri, flag);
-                    else stream_batch<lookup_sorted, true>(lane, bi, ls, ws.bs, cnt, h0, col, tri, flag);
+                int64_t va, vb;
+                load_entry(b + lane, pe, lane, col, twin, hrem, ws.tb, va, vb);
+                __syncwarp();
+                if (MERGE) {
+                    merge_streams(lane, 0, 32, ws.tb, ids, hv, cnt, col, flag);
+                } else if (use_bitmap) {
+                    stream_units<lookup_bitmap, true>(lane, ws.tb, va, vb, lb, cnt, h0, col, tri, flag);
+                    stream_scalars<lookup_bitmap, true>(lane, ws.tb, lb, cnt, h0, col, tri, flag);
+                } else {
+                    stream_units<lookup_sorted, true>(lane, ws.tb, va, vb, ls, cnt, h0, col, tri, flag);
+                    stream_scalars<lookup_sorted, true>(lane, ws.tb, ls, cnt, h0, col, tri, flag);
                 }
-                close_batch(lane, bi.nseg, ws.bs, tri, flag, tv);
+                __syncwarp();
+                close_stream(lane, ws.tb, tri, flag, tv);
+                __syncwarp();
             }
-            __syncwarp();
             for (int i = lane; i < hv; i += 32) {
                 const uint32_t c = cnt[i];
                 if (c) {
@@ -487,39 +513,9 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
 
 // ------------------------------------------------------------- CTA items
 // One CTA per item; the 8 warps share the staged N_H(v).  The item's head
-// entries are taken in rounds of 256 (one batch per warp); inside a round
-// all warps pull groups of whole 32-id chunks from the round's combined
-// chunk space, so that a few long streams do not leave warps idle, and
-// each warp then walks its own batch's remainders.
-template <class LK, bool CNT>
-__device__ __forceinline__ void cta_round_chunks(int lane, int* s_next, const int* s_off,
-                                                 const int* s_nseg, batch_smem* bsm,
-                                                 const LK& lk, uint32_t* cnt, int64_t h0,
-                                                 const int32_t* __restrict__ col,
-                                                 ull* __restrict__ tri, uint8_t* __restrict__ flag) {
-    const int total = s_off[kCtaWarps];
-    for (;;) {
-        int g = 0;
-        if (lane == 0) g = atomicAdd(s_next, 1);
-        g = __shfl_sync(FULL, g, 0);
-        const int c0 = g * kIlp;
-        if (c0 >= total) break;
-        // the group may straddle batches: split it at the owners' boundaries
-        int c = c0;
-        const int c_end = min(c0 + kIlp, total);
-        while (c < c_end) {
-            int w = 0;
-#pragma unroll
-            for (int step = 4; step; step >>= 1)
-                if (w + step < kCtaWarps && s_off[w + step] <= c) w += step;
-            const int stop = min(c_end, s_off[w + 1]);
-            stream_chunks<LK, CNT>(lane, c - s_off[w], stop - s_off[w], s_nseg[w], lk, bsm[w], cnt, h0,
-                                   col, tri, flag);
-            c = stop;
-        }
-    }
-}
-
+// entries are taken in rounds of 256 (a stream table); the round's vector
+// chunks are split evenly over the warps and each lane then reads the head
+// and tail ids of its own stream.
 template <int LOOK, bool MERGE>
 __global__ void __launch_bounds__(TC_CTA_THREADS)
 k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -529,11 +525,8 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             int64_t n_items, ull* __restrict__ cursor, int strategy, ull* __restrict__ tri,
             uint8_t* __restrict__ flag, ull* __restrict__ total) {
     extern __shared__ __align__(16) uint8_t dyn[];
-    __shared__ batch_smem bsm[kCtaWarps];
+    __shared__ __align__(16) stream_table<256> tb;
     __shared__ int64_t s_item;
-    __shared__ int s_next;
-    __shared__ int s_off[kCtaWarps + 1];
-    __shared__ int s_nseg[kCtaWarps];
     __shared__ ull s_tv[kCtaWarps];
     __shared__ uint32_t s_scan[kCtaWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -568,35 +561,39 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             lg = lookup_global{col + h0, hv};
         }
         ull tv = 0;
-        batch_smem& bs = bsm[warp];
-        for (int64_t r0 = pb; r0 < pe; r0 += 32 * kCtaWarps) {
-            const batch_info bi = load_batch(lane, r0 + 32 * warp, pe, col, twin, hrem, bs);
-            if (lane == 0) {
-                s_nseg[warp] = bi.nseg;
-                s_off[warp + 1] = bi.nchunks;
+        for (int64_t r0 = pb; r0 < pe; r0 += 256) {
+            int64_t va, vb;
+            load_entry(r0 + t, pe, t, col, twin, hrem, tb, va, vb);
+            // chunk prefix over the round: warp scan, then warp totals
+            const int nc = (int)((vb - va + 127) >> 7);
+            int incl = nc;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int x = __shfl_up_sync(FULL, incl, d);
+                if (lane >= d) incl += x;
             }
+            if (lane == 31) s_scan[warp] = (uint32_t)incl;
             __syncthreads();
-            if (t == 0) {
-                s_off[0] = 0;
-                for (int k = 1; k <= kCtaWarps; ++k) s_off[k] += s_off[k - 1];
-                s_next = 0;
-            }
+            int before = 0;
+            for (int k = 0; k < warp; ++k) before += (int)s_scan[k];
+            tb.pre[t] = before + incl - nc;
+            if (t == nt - 1) tb.pre[256] = before + incl;
             __syncthreads();
             if (MERGE) {
-                if (bi.nseg > 0) merge_batch(lane, bi.nseg, ls.ids, hv, bs, cnt, col, flag);
+                merge_streams(lane, 32 * warp, 32 * warp + 32, tb, ls.ids, hv, cnt, col, flag);
             } else if (LOOK == L_BITMAP) {
-                cta_round_chunks<lookup_bitmap, true>(lane, &s_next, s_off, s_nseg, bsm, lb, cnt, h0, col, tri, flag);
-                stream_remainders<lookup_bitmap, true>(lane, bi, lb, bs, cnt, h0, col, tri, flag);
+                stream_chunks<lookup_bitmap, true>(lane, warp, tb, lb, cnt, h0, col, tri, flag);
+                stream_scalars<lookup_bitmap, true>(t, tb, lb, cnt, h0, col, tri, flag);
             } else if (LOOK == L_SORTED) {
-                cta_round_chunks<lookup_sorted, true>(lane, &s_next, s_off, s_nseg, bsm, ls, cnt, h0, col, tri, flag);
-                stream_remainders<lookup_sorted, true>(lane, bi, ls, bs, cnt, h0, col, tri, flag);
+                stream_chunks<lookup_sorted, true>(lane, warp, tb, ls, cnt, h0, col, tri, flag);
+                stream_scalars<lookup_sorted, true>(t, tb, ls, cnt, h0, col, tri, flag);
             } else {
-                cta_round_chunks<lookup_global, false>(lane, &s_next, s_off, s_nseg, bsm, lg, nullptr, h0, col, tri, flag);
-                stream_remainders<lookup_global, false>(lane, bi, lg, bs, nullptr, h0, col, tri, flag);
+                stream_chunks<lookup_global, false>(lane, warp, tb, lg, nullptr, h0, col, tri, flag);
+                stream_scalars<lookup_global, false>(t, tb, lg, nullptr, h0, col, tri, flag);
             }
-            __syncthreads();   // every warp's chunks of this round are done
-            close_batch(lane, bi.nseg, bs, tri, flag, tv);
-            __syncthreads();   // before the batches are overwritten
+            __syncthreads();   // every chunk of the round is done
+            close_stream(t, tb, tri, flag, tv);
+            __syncthreads();   // before the table is overwritten
         }
         tv = warp_sum(tv);
         if (lane == 0) s_tv[warp] = tv;
