@@ -171,6 +171,8 @@ typedef struct {
     int64_t items[4];            /* count-step work items per class: bitmap (small shared
                                     footprint), bitmap (large), warp list, CTA list     */
     double  class_bytes[4];      /* algorithmic DRAM bytes of each class's kernel       */
+    double  class_wedges[4];     /* ids streamed by each class                          */
+    double  class_head[4];       /* head entries (lower neighbours) of each class       */
     double  count_bytes;         /* algorithmic DRAM bytes of the whole count step      */
     double  centrality_bytes;    /* algorithmic DRAM bytes of the gather + divide step  */
 } tc_graph_stats;

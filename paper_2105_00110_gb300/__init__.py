@@ -56,6 +56,7 @@ class GraphStats(ctypes.Structure):
                 ("sum_out_degree_sq", ctypes.c_double), ("wedges", ctypes.c_double),
                 ("avg_degeneracy", ctypes.c_double),
                 ("items", ctypes.c_int64 * 4), ("class_bytes", ctypes.c_double * 4),
+                ("class_wedges", ctypes.c_double * 4), ("class_head", ctypes.c_double * 4),
                 ("count_bytes", ctypes.c_double), ("centrality_bytes", ctypes.c_double)]
 
     def as_dict(self):

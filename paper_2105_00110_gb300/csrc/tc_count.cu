@@ -183,8 +183,8 @@ struct stream_table {
     int32_t len[N];
     int32_t u[N];
     uint32_t hits[N];
-    int32_t pre[N + 1];   // prefix of vector work (CTA: 128-id chunks; warp: 4-id units, compacted)
-    int32_t sidx[N];      // warp tables: compacted stream of each unit run
+    int32_t upre[N + 1];  // streams with vector work, compacted: 4-id units before each
+    int32_t cidx[N];      // ... and the table slot of each
 };
 
 // Lane `lane` loads head entry p (if p < pe) into slot i of the table.
@@ -273,10 +273,66 @@ __device__ __forceinline__ void close_stream(int i, stream_table<N>& tb, ull* __
 
 constexpr int kVec = 4;   // 16-byte loads in flight per lane
 
-// Vector spans of a warp's 32 streams as one concatenation of 4-id units,
-// walked lane-consecutively (full lanes even on short streams).  The
-// stream of each lane comes from the mask of stream starts inside the
-// current 32-unit window (one warp OR-reduction).
+// Walks the 4-id units [ub, ue) of the concatenated vector spans of the
+// nc compacted streams of a table, lane-consecutively.  The stream of each
+// lane is found from the starts of the next 32 streams that fall inside
+// the current 32-unit window (one warp OR-reduction); s_base is the
+// stream holding the unit before the window.
+template <class LK, bool CNT, int N>
+__device__ __forceinline__ void walk_units(int lane, stream_table<N>& tb, int nc, int ub, int ue,
+                                           const LK& lk, uint32_t* cnt, int64_t h0,
+                                           const int32_t* __restrict__ col, ull* __restrict__ tri,
+                                           uint8_t* __restrict__ flag) {
+    if (ub >= ue) return;
+    int s_base = -1;
+    if (ub > 0) {   // last stream starting at or before unit ub - 1
+        s_base = 0;
+#pragma unroll
+        for (int step = N / 2; step; step >>= 1)
+            if (s_base + step < nc && tb.upre[s_base + step] <= ub - 1) s_base += step;
+    }
+    const unsigned le = FULL >> (31 - lane);
+    for (int F = ub; F < ue; F += 32 * kVec) {
+        int64_t pos[kVec];
+        int slot[kVec];
+        unsigned smask[kVec];
+        bool ok[kVec];
+        int4 w[kVec];
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+            const int Fj = F + 32 * j;
+            const int cand = s_base + 1 + lane;
+            const int st = cand < nc ? tb.upre[cand] : 0x7fffffff;
+            const unsigned rel = (unsigned)(st - Fj);
+            smask[j] = __reduce_or_sync(FULL, rel < 32u ? (1u << rel) : 0u);
+            const int my = s_base + __popc(smask[j] & le);
+            s_base += __popc(smask[j]);
+            const int q = Fj + lane;
+            ok[j] = q < ue;
+            slot[j] = 0;
+            pos[j] = 0;
+            if (ok[j]) {
+                slot[j] = tb.cidx[my];
+                pos[j] = tb.va[slot[j]] + 4ll * (q - tb.upre[my]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) w[j] = ok[j] ? load4(col, pos[j]) : make_int4(-1, -1, -1, -1);
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) {
+            const uint32_t h = ok[j] ? visit4<LK, CNT>(lk, w[j], pos[j], cnt, h0, tri, flag) : 0u;
+            if ((smask[j] & ~1u) == 0) {
+                // the whole window lies in one stream
+                const uint32_t sum = __reduce_add_sync(FULL, h);
+                if (lane == 0 && sum) atomicAdd(&tb.hits[slot[j]], sum);
+            } else if (h) {
+                atomicAdd(&tb.hits[slot[j]], h);
+            }
+        }
+    }
+}
+
+// Vector spans of a warp's 32 streams (a warp item's batch).
 template <class LK, bool CNT>
 __device__ __forceinline__ void stream_units(int lane, stream_table<32>& tb, int64_t va, int64_t vb,
                                              const LK& lk, uint32_t* cnt, int64_t h0,
@@ -294,90 +350,11 @@ __device__ __forceinline__ void stream_units(int lane, stream_table<32>& tb, int
     if (total == 0) return;
     if (nu > 0) {
         const int k = __popc(nz & ((1u << lane) - 1));
-        tb.pre[k] = incl - nu;
-        tb.sidx[k] = lane;
+        tb.upre[k] = incl - nu;
+        tb.cidx[k] = lane;
     }
     __syncwarp();
-    const int nrun = __popc(nz);
-    const int my_excl = lane < nrun ? tb.pre[lane] : 0x7fffffff;
-    const unsigned le = FULL >> (31 - lane);
-    int s0 = -1;
-    for (int F = 0; F < total; F += 32 * kVec) {
-        int64_t pos[kVec];
-        int seg[kVec];
-        unsigned smask[kVec];
-        bool ok[kVec];
-        int4 w[kVec];
-#pragma unroll
-        for (int j = 0; j < kVec; ++j) {
-            const int Fj = F + 32 * j;
-            const int rel = my_excl - Fj;
-            smask[j] = __reduce_or_sync(FULL, (rel >= 0 && rel < 32) ? (1u << rel) : 0u);
-            seg[j] = s0 + __popc(smask[j] & le);
-            s0 += __popc(smask[j]);
-            const int q = Fj + lane;
-            ok[j] = q < total;
-            pos[j] = ok[j] ? tb.va[tb.sidx[seg[j]]] + 4ll * (q - tb.pre[seg[j]]) : 0;
-        }
-#pragma unroll
-        for (int j = 0; j < kVec; ++j) w[j] = ok[j] ? load4(col, pos[j]) : make_int4(-1, -1, -1, -1);
-#pragma unroll
-        for (int j = 0; j < kVec; ++j) {
-            const uint32_t h = ok[j] ? visit4<LK, CNT>(lk, w[j], pos[j], cnt, h0, tri, flag) : 0u;
-            if ((smask[j] & ~1u) == 0) {
-                // the whole window lies in one stream
-                const uint32_t sum = __reduce_add_sync(FULL, h);
-                if (lane == 0 && sum) atomicAdd(&tb.hits[tb.sidx[seg[j]]], sum);
-            } else if (h) {
-                atomicAdd(&tb.hits[tb.sidx[seg[j]]], h);
-            }
-        }
-    }
-}
-
-// Vector work of a CTA round: the round's 256 streams cut into 128-id
-// chunks (32 lanes x 4 ids, the last chunk of a stream partial); warp w
-// takes the contiguous chunk range [T w / 8, T (w+1) / 8) and walks it
-// stream by stream.
-template <class LK, bool CNT>
-__device__ __forceinline__ void stream_chunks(int lane, int warp, stream_table<256>& tb, const LK& lk,
-                                              uint32_t* cnt, int64_t h0, const int32_t* __restrict__ col,
-                                              ull* __restrict__ tri, uint8_t* __restrict__ flag) {
-    const int T = tb.pre[256];
-    const int cb = (int)(((int64_t)T * warp) >> 3), ce = (int)(((int64_t)T * (warp + 1)) >> 3);
-    if (cb >= ce) return;
-    int s = 0;   // last stream whose first chunk is at or before cb
-#pragma unroll
-    for (int step = 128; step; step >>= 1)
-        if (tb.pre[s + step] <= cb) s += step;
-    int k = cb - tb.pre[s];
-    for (int c = cb; c < ce; c += kVec) {
-        int64_t pos[kVec], lim[kVec];
-        int si[kVec];
-        int4 w[kVec];
-#pragma unroll
-        for (int j = 0; j < kVec; ++j) {
-            si[j] = s;
-            pos[j] = tb.va[s] + 128ll * k + 4 * lane;
-            lim[j] = (c + j < ce) ? tb.vb[s] : 0;
-            // advance to the next chunk (uniform across the warp)
-            if (c + j + 1 < ce) {
-                ++k;
-                while (k >= tb.pre[s + 1] - tb.pre[s]) {
-                    k = 0;
-                    ++s;
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kVec; ++j) w[j] = pos[j] < lim[j] ? load4(col, pos[j]) : make_int4(-1, -1, -1, -1);
-#pragma unroll
-        for (int j = 0; j < kVec; ++j) {
-            const uint32_t h = pos[j] < lim[j] ? visit4<LK, CNT>(lk, w[j], pos[j], cnt, h0, tri, flag) : 0u;
-            const uint32_t sum = __reduce_add_sync(FULL, h);
-            if (lane == 0 && sum) atomicAdd(&tb.hits[si[j]], sum);
-        }
-    }
+    walk_units<LK, CNT, 32>(lane, tb, __popc(nz), 0, total, lk, cnt, h0, col, tri, flag);
 }
 
 // Merge-path intersection of the staged A = N_H(v) (shared, ascending)
@@ -529,6 +506,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
     __shared__ int64_t s_item;
     __shared__ ull s_tv[kCtaWarps];
     __shared__ uint32_t s_scan[kCtaWarps];
+    __shared__ int s_cnt[kCtaWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t = threadIdx.x, nt = TC_CTA_THREADS;
     auto cbar = [] { __syncthreads(); };
@@ -564,34 +542,52 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         for (int64_t r0 = pb; r0 < pe; r0 += 256) {
             int64_t va, vb;
             load_entry(r0 + t, pe, t, col, twin, hrem, tb, va, vb);
-            // chunk prefix over the round: warp scan, then warp totals
-            const int nc = (int)((vb - va + 127) >> 7);
-            int incl = nc;
+            // compact the streams with vector work over the round: warp
+            // scans of the unit counts, then the warp totals
+            const int nu = (int)((vb - va) >> 2);
+            const unsigned nz = __ballot_sync(FULL, nu > 0);
+            int incl = nu;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const int x = __shfl_up_sync(FULL, incl, d);
                 if (lane >= d) incl += x;
             }
-            if (lane == 31) s_scan[warp] = (uint32_t)incl;
+            if (lane == 31) {
+                s_scan[warp] = (uint32_t)incl;
+                s_cnt[warp] = __popc(nz);
+            }
             __syncthreads();
-            int before = 0;
-            for (int k = 0; k < warp; ++k) before += (int)s_scan[k];
-            tb.pre[t] = before + incl - nc;
-            if (t == nt - 1) tb.pre[256] = before + incl;
+            int before_u = 0, before_c = 0, U = 0, NC = 0;
+            for (int k = 0; k < kCtaWarps; ++k) {
+                if (k < warp) {
+                    before_u += (int)s_scan[k];
+                    before_c += s_cnt[k];
+                }
+                U += (int)s_scan[k];
+                NC += s_cnt[k];
+            }
+            if (nu > 0) {
+                const int k = before_c + __popc(nz & ((1u << lane) - 1));
+                tb.upre[k] = before_u + incl - nu;
+                tb.cidx[k] = t;
+            }
             __syncthreads();
             if (MERGE) {
                 merge_streams(lane, 32 * warp, 32 * warp + 32, tb, ls.ids, hv, cnt, col, flag);
-            } else if (LOOK == L_BITMAP) {
-                stream_chunks<lookup_bitmap, true>(lane, warp, tb, lb, cnt, h0, col, tri, flag);
-                stream_scalars<lookup_bitmap, true>(t, tb, lb, cnt, h0, col, tri, flag);
-            } else if (LOOK == L_SORTED) {
-                stream_chunks<lookup_sorted, true>(lane, warp, tb, ls, cnt, h0, col, tri, flag);
-                stream_scalars<lookup_sorted, true>(t, tb, ls, cnt, h0, col, tri, flag);
             } else {
-                stream_chunks<lookup_global, false>(lane, warp, tb, lg, nullptr, h0, col, tri, flag);
-                stream_scalars<lookup_global, false>(t, tb, lg, nullptr, h0, col, tri, flag);
+                const int ub = (int)(((int64_t)U * warp) >> 3), ue = (int)(((int64_t)U * (warp + 1)) >> 3);
+                if (LOOK == L_BITMAP) {
+                    walk_units<lookup_bitmap, true, 256>(lane, tb, NC, ub, ue, lb, cnt, h0, col, tri, flag);
+                    stream_scalars<lookup_bitmap, true>(t, tb, lb, cnt, h0, col, tri, flag);
+                } else if (LOOK == L_SORTED) {
+                    walk_units<lookup_sorted, true, 256>(lane, tb, NC, ub, ue, ls, cnt, h0, col, tri, flag);
+                    stream_scalars<lookup_sorted, true>(t, tb, ls, cnt, h0, col, tri, flag);
+                } else {
+                    walk_units<lookup_global, false, 256>(lane, tb, NC, ub, ue, lg, nullptr, h0, col, tri, flag);
+                    stream_scalars<lookup_global, false>(t, tb, lg, nullptr, h0, col, tri, flag);
+                }
             }
-            __syncthreads();   // every chunk of the round is done
+            __syncthreads();   // every unit of the round is done
             close_stream(t, tb, tri, flag, tv);
             __syncthreads();   // before the table is overwritten
         }
@@ -813,6 +809,8 @@ tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s) {
     for (int c = 0; c < TC_NUM_CLS; ++c) {
         S.items[c] = p.count[c];
         S.class_bytes[c] = 4.0 * (double)h.staged[c] + 16.0 * (double)h.head[c] + 4.0 * (double)h.wedges[c];
+        S.class_wedges[c] = (double)h.wedges[c];
+        S.class_head[c] = (double)h.head[c];
     }
     cleanup();
     PLAN_CUDA(cudaStreamSynchronize(s));
