@@ -61,7 +61,7 @@ def peaks():
 
 # --------------------------------------------------------------- clocks
 class ClockSampler:
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -80,7 +80,9 @@ class ClockSampler:
         except Exception:
             self.proc = None
 
-    def stop(self) -> dict:
+    def stop(self, t0: float | None = None, t1: float | None = None) -> dict:
+        """Stops sampling; keeps the samples taken between host times t0 and
+        t1 (the timed region) when there are any."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -93,38 +95,27 @@ class ClockSampler:
         rows = [r.strip().split(",") for r in self.f.read().splitlines() if r.strip()]
         self.f.close()
         os.unlink(self.f.name)
-        sm, smax, power, reasons = [], [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
+        samples = []
         for r in rows:
             try:
-                sm.append(float(r[1]))
-                smax.append(float(r[2]))
-                power.append(float(r[3]))
-                for k, name in enumerate(names):
-                    if r[5 + k].strip().lower().startswith("active"):
-                        reasons.add(name)
+                ts = datetime.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                samples.append((ts, float(r[2]), float(r[3]), float(r[4]), [x.strip() for x in r[6:10]]))
             except (ValueError, IndexError):
                 continue
-        # samples under load: the SM clock is read while kernels run; the
-        # median is over every sample taken inside the timed region
+        inside = [x for x in samples if t0 is not None and t0 <= x[0] <= t1]
+        use = inside if inside else samples
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for x in use:
+            for k, name in enumerate(names):
+                if x[4][k].lower().startswith("active"):
+                    reasons.add(name)
+        sm = [x[1] for x in use]
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "power_w_max": max(power) if power else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
-
-
-def aggregate(t_ms: float, e2e_ms: float, units: int, e2e_units: int, world: int, device=None):
-    """Whole-job figures across ranks: the slowest rank's time (MAX) and the
-    units all ranks processed (SUM).  Identity for a single process."""
-    if world <= 1:
-        return t_ms, e2e_ms, units, e2e_units
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([t_ms, e2e_ms], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    u = torch.tensor([float(units), float(e2e_units)], dtype=torch.float64, device=device)
-    dist.all_reduce(u, op=dist.ReduceOp.SUM)
-    return float(t[0]), float(t[1]), int(u[0]), int(u[1])
+                "sm_max_mhz": max(x[2] for x in use) if use else None,
+                "power_w_max": max(x[3] for x in use) if use else None,
+                "samples": len(use), "in_timed_region": bool(inside), "reasons": sorted(reasons)}
 
 
 # ------------------------------------------------------------ our path
@@ -183,15 +174,18 @@ def run_ours(args, spec, wl_name):
         torch.cuda.synchronize(dev)
 
     # ---------------- device-resident timing
+    # the clock sampler starts before the warm-up so that its start-up does
+    # not fall into the timed region; only samples inside it are kept
+    sampler = ClockSampler(local)
+    sampler.start()
     for _ in range(args.warmup):
         m, total = step(d_src, d_dst)
     stats = stats_box[0]
     tcg.tc_profile_reset()
     tcg.tc_profile_enable(True)
     launches0 = tcg.tc_launch_count()
-    sampler = ClockSampler(local)
-    sampler.start()
     barrier()
+    host_t0 = time.time()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -201,7 +195,8 @@ def run_ours(args, spec, wl_name):
         edges += m
     ev1.record(stream)
     barrier()
-    clocks = sampler.stop()
+    host_t1 = time.time()
+    clocks = sampler.stop(host_t0, host_t1)
     tcg.tc_profile_enable(False)
     launches = tcg.tc_launch_count() - launches0
     prof = tcg.tc_profile_read()

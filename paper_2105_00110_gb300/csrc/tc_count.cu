@@ -232,11 +232,29 @@ __device__ __forceinline__ uint32_t visit(const LK& lk, int32_t w, int64_t pos, 
     return 1;
 }
 
+// The 4 ids of a 4-aligned unit at pos: counts as visit(), and the flags
+// of the unit's hits set with one 32-bit OR (the unit's 4 flag bytes form
+// one aligned word; an OR never clears a flag another thread set).
 template <class LK, bool CNT>
 __device__ __forceinline__ uint32_t visit4(const LK& lk, int4 w, int64_t pos, uint32_t* cnt, int64_t h0,
                                            ull* __restrict__ tri, uint8_t* __restrict__ flag) {
-    return visit<LK, CNT>(lk, w.x, pos, cnt, h0, tri, flag) + visit<LK, CNT>(lk, w.y, pos + 1, cnt, h0, tri, flag) +
-           visit<LK, CNT>(lk, w.z, pos + 2, cnt, h0, tri, flag) + visit<LK, CNT>(lk, w.w, pos + 3, cnt, h0, tri, flag);
+    const int32_t ws[4] = {w.x, w.y, w.z, w.w};
+    uint32_t bits = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int l = 0;
+        if (lk.find(ws[q], l)) {
+            if (CNT) {
+                atomicAdd(&cnt[l], 1u);
+            } else {
+                atomicAdd(&tri[ws[q]], 1ull);
+                flag[h0 + l] = 1;
+            }
+            bits |= 1u << (8 * q);
+        }
+    }
+    if (bits) atomicOr(reinterpret_cast<unsigned int*>(flag + pos), bits);
+    return (uint32_t)__popc(bits);
 }
 
 __device__ __forceinline__ int4 load4(const int32_t* __restrict__ col, int64_t pos) {
@@ -271,7 +289,7 @@ __device__ __forceinline__ void close_stream(int i, stream_table<N>& tb, ull* __
     }
 }
 
-constexpr int kVec = 4;   // 16-byte loads in flight per lane
+constexpr int kVec = 2;   // 16-byte loads per lane per group (two groups in flight)
 
 // Walks the 4-id units [ub, ue) of the concatenated vector spans of the
 // nc compacted streams of a table, lane-consecutively.  The stream of each
@@ -292,43 +310,57 @@ __device__ __forceinline__ void walk_units(int lane, stream_table<N>& tb, int nc
             if (s_base + step < nc && tb.upre[s_base + step] <= ub - 1) s_base += step;
     }
     const unsigned le = FULL >> (31 - lane);
-    for (int F = ub; F < ue; F += 32 * kVec) {
-        int64_t pos[kVec];
-        int slot[kVec];
-        unsigned smask[kVec];
-        bool ok[kVec];
-        int4 w[kVec];
+    // one group = kVec windows of 32 units; the loads of group g+1 are in
+    // flight while group g is looked up
+    int64_t pos[2][kVec];
+    int slot[2][kVec];
+    unsigned smask[2][kVec];
+    bool ok[2][kVec];
+    int4 w[2][kVec];
+    auto describe = [&](int b, int F) {
 #pragma unroll
         for (int j = 0; j < kVec; ++j) {
             const int Fj = F + 32 * j;
             const int cand = s_base + 1 + lane;
             const int st = cand < nc ? tb.upre[cand] : 0x7fffffff;
             const unsigned rel = (unsigned)(st - Fj);
-            smask[j] = __reduce_or_sync(FULL, rel < 32u ? (1u << rel) : 0u);
-            const int my = s_base + __popc(smask[j] & le);
-            s_base += __popc(smask[j]);
+            smask[b][j] = __reduce_or_sync(FULL, rel < 32u ? (1u << rel) : 0u);
+            const int my = s_base + __popc(smask[b][j] & le);
+            s_base += __popc(smask[b][j]);
             const int q = Fj + lane;
-            ok[j] = q < ue;
-            slot[j] = 0;
-            pos[j] = 0;
-            if (ok[j]) {
-                slot[j] = tb.cidx[my];
-                pos[j] = tb.va[slot[j]] + 4ll * (q - tb.upre[my]);
+            ok[b][j] = q < ue;
+            slot[b][j] = 0;
+            pos[b][j] = 0;
+            if (ok[b][j]) {
+                slot[b][j] = tb.cidx[my];
+                pos[b][j] = tb.va[slot[b][j]] + 4ll * (q - tb.upre[my]);
             }
         }
 #pragma unroll
-        for (int j = 0; j < kVec; ++j) w[j] = ok[j] ? load4(col, pos[j]) : make_int4(-1, -1, -1, -1);
+        for (int j = 0; j < kVec; ++j) w[b][j] = ok[b][j] ? load4(col, pos[b][j]) : make_int4(-1, -1, -1, -1);
+    };
+    auto process = [&](int b) {
 #pragma unroll
         for (int j = 0; j < kVec; ++j) {
-            const uint32_t h = ok[j] ? visit4<LK, CNT>(lk, w[j], pos[j], cnt, h0, tri, flag) : 0u;
-            if ((smask[j] & ~1u) == 0) {
+            const uint32_t h = ok[b][j] ? visit4<LK, CNT>(lk, w[b][j], pos[b][j], cnt, h0, tri, flag) : 0u;
+            if ((smask[b][j] & ~1u) == 0) {
                 // the whole window lies in one stream
                 const uint32_t sum = __reduce_add_sync(FULL, h);
-                if (lane == 0 && sum) atomicAdd(&tb.hits[slot[j]], sum);
+                if (lane == 0 && sum) atomicAdd(&tb.hits[slot[b][j]], sum);
             } else if (h) {
-                atomicAdd(&tb.hits[slot[j]], h);
+                atomicAdd(&tb.hits[slot[b][j]], h);
             }
         }
+    };
+    // buffers 0 and 1 alternate with compile-time indices
+    constexpr int G = 32 * kVec;
+    describe(0, ub);
+    for (int F = ub; F < ue; F += 2 * G) {
+        if (F + G < ue) describe(1, F + G);
+        process(0);
+        if (F + G >= ue) break;
+        if (F + 2 * G < ue) describe(0, F + 2 * G);
+        process(1);
     }
 }
 
@@ -414,7 +446,7 @@ __device__ __forceinline__ bool warp_bitmap_fits(int64_t words, int64_t hv) {
 }
 
 template <bool MERGE>
-__global__ void __launch_bounds__(TC_CTA_THREADS)
+__global__ void __launch_bounds__(TC_CTA_THREADS, 3)
 k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
              const int64_t* __restrict__ hstart, const int64_t* __restrict__ twin,
              const int32_t* __restrict__ hrem, const int32_t* __restrict__ it_v,
