@@ -118,6 +118,20 @@ class ClockSampler:
                 "samples": len(use), "in_timed_region": bool(inside), "reasons": sorted(reasons)}
 
 
+def aggregate(t_ms: float, e2e_ms: float, units: int, e2e_units: int, world: int, device=None):
+    """Whole-job figures across ranks: the slowest rank's time (MAX) and the
+    units all ranks processed (SUM).  Identity for a single process."""
+    if world <= 1:
+        return t_ms, e2e_ms, units, e2e_units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_ms, e2e_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units), float(e2e_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), int(u[0]), int(u[1])
+
+
 # ------------------------------------------------------------ our path
 def run_ours(args, spec, wl_name):
     import numpy as np
