@@ -170,87 +170,92 @@ __device__ __forceinline__ lookup_bitmap build_bitmap(int t, int nt, uint8_t* re
 }
 
 // ------------------------------------------------------------ streams
-// A batch of head entries (lower neighbours u of the item's middle vertex v)
-// is a table of streams: stream i is col[p0, p0 + len), the part of N_H(u)
-// above v.  Its 4-aligned interior [va, vb) is read with 16-byte vector
-// loads (4 ids per lane); the at most 6 ids outside it (head and tail) are
-// read one by one by the lane that owns the stream.
+// A batch of head entries (lower neighbours u of the item's middle vertex
+// v) is a table of streams: stream i is col[p0, p0 + len), the part of
+// N_H(u) above v (p0 = twin(u,v) + 1).  Every stream is read as whole
+// 4-aligned units [p0 & ~3, (p0 + len + 3) & ~3) with 16-byte vector loads;
+// the ids of its first and last unit that lie outside it are masked.
 template <int N>
 struct stream_table {
-    int64_t p0[N];
-    int64_t va[N];
-    int64_t vb[N];
-    int32_t len[N];
+    int64_t va[N];        // first unit of the stream (4-aligned position)
+    int32_t fl[N];        // (len << 2) | (p0 - va)
     int32_t u[N];
     uint32_t hits[N];
-    int32_t upre[N + 1];  // streams with vector work, compacted: 4-id units before each
+    int32_t upre[N + 1];  // non-empty streams, compacted: units before each
     int32_t cidx[N];      // ... and the table slot of each
 };
 
-// Lane `lane` loads head entry p (if p < pe) into slot i of the table.
-template <int N>
-__device__ __forceinline__ void load_entry(int64_t p, int64_t pe, int i,
-                                           const int32_t* __restrict__ col,
-                                           const int64_t* __restrict__ twin,
-                                           const int32_t* __restrict__ hrem, stream_table<N>& tb,
-                                           int64_t& va, int64_t& vb) {
-    int r = 0;
-    int64_t p0 = 0;
-    int32_t u = 0;
+// A head entry as loaded from global memory.
+struct entry {
+    int r;         // stream length hrem
+    int32_t u;     // the lower neighbour
+    int64_t t;     // twin(u, v)
+};
+
+__device__ __forceinline__ entry fetch_entry(int64_t p, int64_t pe, const int32_t* __restrict__ col,
+                                             const int64_t* __restrict__ twin,
+                                             const int32_t* __restrict__ hrem) {
+    entry e{0, 0, 0};
     if (p < pe) {
-        r = hrem[p];
-        if (r > 0) {
-            p0 = twin[p] + 1;
-            u = col[p];
-        }
+        e.r = hrem[p];
+        e.t = twin[p];
+        e.u = col[p];
     }
-    va = (p0 + 3) & ~3ll;
-    vb = (p0 + r) & ~3ll;
-    if (r == 0 || va >= vb) va = vb = 0;
-    tb.p0[i] = p0;
+    return e;
+}
+
+// Puts an entry into slot i; returns its number of 4-id units.
+template <int N>
+__device__ __forceinline__ int put_entry(const entry& e, int i, stream_table<N>& tb) {
+    int nu = 0, fl = 0;
+    int64_t va = 0;
+    if (e.r > 0) {
+        const int64_t p0 = e.t + 1;
+        va = p0 & ~3ll;
+        nu = (int)((((p0 + e.r + 3) & ~3ll) - va) >> 2);
+        fl = (e.r << 2) | (int)(p0 - va);
+    }
     tb.va[i] = va;
-    tb.vb[i] = vb;
-    tb.len[i] = r;
-    tb.u[i] = u;
+    tb.fl[i] = fl;
+    tb.u[i] = e.u;
     tb.hits[i] = 0;
+    return nu;
 }
 
-// One streamed id at position pos: look it up; on a hit count the
-// triangle (u, v, w) at the staged index and flag the edge (u, w).
-template <class LK, bool CNT>
-__device__ __forceinline__ uint32_t visit(const LK& lk, int32_t w, int64_t pos, uint32_t* cnt, int64_t h0,
-                                          ull* __restrict__ tri, uint8_t* __restrict__ flag) {
-    int l = 0;
-    if (!lk.find(w, l)) return 0;
-    if (CNT) {
-        atomicAdd(&cnt[l], 1u);
-    } else {
-        atomicAdd(&tri[w], 1ull);
-        flag[h0 + l] = 1;
+// Credits the hits of stream i to △(u) and flags the edge (u, v).
+template <int N>
+__device__ __forceinline__ void close_stream(int i, stream_table<N>& tb, ull* __restrict__ tri,
+                                             uint8_t* __restrict__ flag, ull& tv) {
+    const uint32_t c = tb.hits[i];
+    if (c) {
+        atomicAdd(&tri[tb.u[i]], (ull)c);
+        flag[tb.va[i] + (tb.fl[i] & 3) - 1] = 1;   // twin(u, v): the canonical entry of (u, v)
+        tv += c;
     }
-    flag[pos] = 1;
-    return 1;
 }
 
-// The 4 ids of a 4-aligned unit at pos: counts as visit(), and the flags
-// of the unit's hits set with one 32-bit OR (the unit's 4 flag bytes form
-// one aligned word; an OR never clears a flag another thread set).
+// The ids of one unit at pos whose offsets off+k (k = 0..3) from the
+// stream start lie in [0, len): look each up; on a hit count the triangle
+// (u, v, w) at the staged index; set the unit's hit flags with one 32-bit
+// OR (the unit's 4 flag bytes form one aligned word, and an OR never clears
+// a flag another thread set).  Returns the number of hits.
 template <class LK, bool CNT>
-__device__ __forceinline__ uint32_t visit4(const LK& lk, int4 w, int64_t pos, uint32_t* cnt, int64_t h0,
-                                           ull* __restrict__ tri, uint8_t* __restrict__ flag) {
+__device__ __forceinline__ uint32_t visit_unit(const LK& lk, int4 w, int64_t pos, int off, int len,
+                                               uint32_t* cnt, int64_t h0, ull* __restrict__ tri,
+                                               uint8_t* __restrict__ flag) {
     const int32_t ws[4] = {w.x, w.y, w.z, w.w};
     uint32_t bits = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int k = 0; k < 4; ++k) {
         int l = 0;
-        if (lk.find(ws[q], l)) {
+        if ((unsigned)(off + k) < (unsigned)len && lk.find(ws[k], l)) {
             if (CNT) {
                 atomicAdd(&cnt[l], 1u);
             } else {
-                atomicAdd(&tri[ws[q]], 1ull);
+                atomicAdd(&tri[ws[k]], 1ull);
                 flag[h0 + l] = 1;
             }
-            bits |= 1u << (8 * q);
+            bits |= 1u << (8 * k);
         }
     }
     if (bits) atomicOr(reinterpret_cast<unsigned int*>(flag + pos), bits);
@@ -261,38 +266,16 @@ __device__ __forceinline__ int4 load4(const int32_t* __restrict__ col, int64_t p
     return __ldg(reinterpret_cast<const int4*>(col + pos));
 }
 
-// The head and tail ids of stream i (outside its vector span), by one lane.
-template <class LK, bool CNT, int N>
-__device__ __forceinline__ void stream_scalars(int i, stream_table<N>& tb, const LK& lk, uint32_t* cnt,
-                                               int64_t h0, const int32_t* __restrict__ col,
-                                               ull* __restrict__ tri, uint8_t* __restrict__ flag) {
-    const int r = tb.len[i];
-    if (r == 0) return;
-    const int64_t p0 = tb.p0[i], va = tb.va[i], vb = tb.vb[i], pend = p0 + r;
-    const int64_t end1 = va < vb ? va : pend;
-    uint32_t h = 0;
-    for (int64_t e = p0; e < end1; ++e) h += visit<LK, CNT>(lk, __ldg(col + e), e, cnt, h0, tri, flag);
-    if (va < vb)
-        for (int64_t e = vb; e < pend; ++e) h += visit<LK, CNT>(lk, __ldg(col + e), e, cnt, h0, tri, flag);
-    if (h) atomicAdd(&tb.hits[i], h);
-}
+#ifndef TC_UNITS_IN_FLIGHT
+#define TC_UNITS_IN_FLIGHT 4
+#endif
+#ifndef TC_CTA_MIN_BLOCKS
+#define TC_CTA_MIN_BLOCKS 4
+#endif
+constexpr int kVec = TC_UNITS_IN_FLIGHT;   // 16-byte loads in flight per lane
 
-// Credits the hits of stream i to △(u) and flags the edge (u, v).
-template <int N>
-__device__ __forceinline__ void close_stream(int i, stream_table<N>& tb, ull* __restrict__ tri,
-                                             uint8_t* __restrict__ flag, ull& tv) {
-    const uint32_t c = tb.hits[i];
-    if (c) {
-        atomicAdd(&tri[tb.u[i]], (ull)c);
-        flag[tb.p0[i] - 1] = 1;   // twin(u, v): the canonical entry of (u, v)
-        tv += c;
-    }
-}
-
-constexpr int kVec = 2;   // 16-byte loads per lane per group (two groups in flight)
-
-// Walks the 4-id units [ub, ue) of the concatenated vector spans of the
-// nc compacted streams of a table, lane-consecutively.  The stream of each
+// Walks the units [ub, ue) of the concatenated streams of a table (its nc
+// compacted non-empty streams), lane-consecutively.  The stream of each
 // lane is found from the starts of the next 32 streams that fall inside
 // the current 32-unit window (one warp OR-reduction); s_base is the
 // stream holding the unit before the window.
@@ -310,83 +293,50 @@ __device__ __forceinline__ void walk_units(int lane, stream_table<N>& tb, int nc
             if (s_base + step < nc && tb.upre[s_base + step] <= ub - 1) s_base += step;
     }
     const unsigned le = FULL >> (31 - lane);
-    // one group = kVec windows of 32 units; the loads of group g+1 are in
-    // flight while group g is looked up
-    int64_t pos[2][kVec];
-    int slot[2][kVec];
-    unsigned smask[2][kVec];
-    bool ok[2][kVec];
-    int4 w[2][kVec];
-    auto describe = [&](int b, int F) {
+    for (int F = ub; F < ue; F += 32 * kVec) {
+        int64_t pos[kVec];
+        int slot[kVec], off[kVec], len[kVec];
+        unsigned smask[kVec];
+        bool ok[kVec];
+        int4 w[kVec];
 #pragma unroll
         for (int j = 0; j < kVec; ++j) {
             const int Fj = F + 32 * j;
             const int cand = s_base + 1 + lane;
             const int st = cand < nc ? tb.upre[cand] : 0x7fffffff;
             const unsigned rel = (unsigned)(st - Fj);
-            smask[b][j] = __reduce_or_sync(FULL, rel < 32u ? (1u << rel) : 0u);
-            const int my = s_base + __popc(smask[b][j] & le);
-            s_base += __popc(smask[b][j]);
+            smask[j] = __reduce_or_sync(FULL, rel < 32u ? (1u << rel) : 0u);
+            const int my = s_base + __popc(smask[j] & le);
+            s_base += __popc(smask[j]);
             const int q = Fj + lane;
-            ok[b][j] = q < ue;
-            slot[b][j] = 0;
-            pos[b][j] = 0;
-            if (ok[b][j]) {
-                slot[b][j] = tb.cidx[my];
-                pos[b][j] = tb.va[slot[b][j]] + 4ll * (q - tb.upre[my]);
+            ok[j] = q < ue;
+            slot[j] = 0;
+            pos[j] = 0;
+            off[j] = 0;
+            len[j] = 0;
+            if (ok[j]) {
+                slot[j] = tb.cidx[my];
+                const int uo = q - tb.upre[my];
+                const int f = tb.fl[slot[j]];
+                pos[j] = tb.va[slot[j]] + 4ll * uo;
+                off[j] = 4 * uo - (f & 3);
+                len[j] = f >> 2;
             }
         }
 #pragma unroll
-        for (int j = 0; j < kVec; ++j) w[b][j] = ok[b][j] ? load4(col, pos[b][j]) : make_int4(-1, -1, -1, -1);
-    };
-    auto process = [&](int b) {
+        for (int j = 0; j < kVec; ++j) w[j] = ok[j] ? load4(col, pos[j]) : make_int4(-1, -1, -1, -1);
 #pragma unroll
         for (int j = 0; j < kVec; ++j) {
-            const uint32_t h = ok[b][j] ? visit4<LK, CNT>(lk, w[b][j], pos[b][j], cnt, h0, tri, flag) : 0u;
-            if ((smask[b][j] & ~1u) == 0) {
+            const uint32_t h = ok[j] ? visit_unit<LK, CNT>(lk, w[j], pos[j], off[j], len[j], cnt, h0, tri, flag) : 0u;
+            if ((smask[j] & ~1u) == 0) {
                 // the whole window lies in one stream
                 const uint32_t sum = __reduce_add_sync(FULL, h);
-                if (lane == 0 && sum) atomicAdd(&tb.hits[slot[b][j]], sum);
+                if (lane == 0 && sum) atomicAdd(&tb.hits[slot[j]], sum);
             } else if (h) {
-                atomicAdd(&tb.hits[slot[b][j]], h);
+                atomicAdd(&tb.hits[slot[j]], h);
             }
         }
-    };
-    // buffers 0 and 1 alternate with compile-time indices
-    constexpr int G = 32 * kVec;
-    describe(0, ub);
-    for (int F = ub; F < ue; F += 2 * G) {
-        if (F + G < ue) describe(1, F + G);
-        process(0);
-        if (F + G >= ue) break;
-        if (F + 2 * G < ue) describe(0, F + 2 * G);
-        process(1);
     }
-}
-
-// Vector spans of a warp's 32 streams (a warp item's batch).
-template <class LK, bool CNT>
-__device__ __forceinline__ void stream_units(int lane, stream_table<32>& tb, int64_t va, int64_t vb,
-                                             const LK& lk, uint32_t* cnt, int64_t h0,
-                                             const int32_t* __restrict__ col, ull* __restrict__ tri,
-                                             uint8_t* __restrict__ flag) {
-    const int nu = (int)((vb - va) >> 2);
-    const unsigned nz = __ballot_sync(FULL, nu > 0);
-    int incl = nu;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int x = __shfl_up_sync(FULL, incl, d);
-        if (lane >= d) incl += x;
-    }
-    const int total = __shfl_sync(FULL, incl, 31);
-    if (total == 0) return;
-    if (nu > 0) {
-        const int k = __popc(nz & ((1u << lane) - 1));
-        tb.upre[k] = incl - nu;
-        tb.cidx[k] = lane;
-    }
-    __syncwarp();
-    walk_units<LK, CNT, 32>(lane, tb, __popc(nz), 0, total, lk, cnt, h0, col, tri, flag);
 }
 
 // Merge-path intersection of the staged A = N_H(v) (shared, ascending)
@@ -400,9 +350,9 @@ __device__ __forceinline__ void merge_streams(int lane, int i0, int i1, stream_t
                                               const int32_t* __restrict__ col,
                                               uint8_t* __restrict__ flag) {
     for (int i = i0; i < i1; ++i) {
-        const int nb = tb.len[i];
+        const int nb = tb.fl[i] >> 2;
         if (nb == 0) continue;
-        const int64_t p0 = tb.p0[i];
+        const int64_t p0 = tb.va[i] + (tb.fl[i] & 3);
         const int32_t* B = col + p0;
         const int L = na + nb;
         const int d0 = (int)(((int64_t)L * lane) >> 5), d1 = (int)(((int64_t)L * (lane + 1)) >> 5);
@@ -445,6 +395,26 @@ __device__ __forceinline__ bool warp_bitmap_fits(int64_t words, int64_t hv) {
     return hv < 65536 && bitmap_bytes(words, hv) <= kWarpSmem;
 }
 
+// Compacts the non-empty streams of a warp's 32-entry table; returns the
+// total number of units.
+__device__ __forceinline__ int compact_warp(int lane, int nu, stream_table<32>& tb, int& nc) {
+    const unsigned nz = __ballot_sync(FULL, nu > 0);
+    int incl = nu;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int x = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += x;
+    }
+    if (nu > 0) {
+        const int k = __popc(nz & ((1u << lane) - 1));
+        tb.upre[k] = incl - nu;
+        tb.cidx[k] = lane;
+    }
+    nc = __popc(nz);
+    __syncwarp();
+    return __shfl_sync(FULL, incl, 31);
+}
+
 template <bool MERGE>
 __global__ void __launch_bounds__(TC_CTA_THREADS, 3)
 k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -468,6 +438,7 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
         for (int64_t it = base; it < lim; ++it) {
             const int32_t v = it_v[it];
             const int64_t pb = it_pb[it], pe = it_pe[it];
+            entry nxt = fetch_entry(pb + lane, pe, col, twin, hrem);
             const int64_t h0 = hstart[v], h1 = row_ptr[v + 1];
             const int hv = (int)(h1 - h0);
             const int32_t nbits = col[h1 - 1] - v;
@@ -488,18 +459,13 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
             const lookup_sorted ls{ids, hv};
             ull tv = 0;
             for (int64_t b = pb; b < pe; b += 32) {
-                int64_t va, vb;
-                load_entry(b + lane, pe, lane, col, twin, hrem, ws.tb, va, vb);
-                __syncwarp();
-                if (MERGE) {
-                    merge_streams(lane, 0, 32, ws.tb, ids, hv, cnt, col, flag);
-                } else if (use_bitmap) {
-                    stream_units<lookup_bitmap, true>(lane, ws.tb, va, vb, lb, cnt, h0, col, tri, flag);
-                    stream_scalars<lookup_bitmap, true>(lane, ws.tb, lb, cnt, h0, col, tri, flag);
-                } else {
-                    stream_units<lookup_sorted, true>(lane, ws.tb, va, vb, ls, cnt, h0, col, tri, flag);
-                    stream_scalars<lookup_sorted, true>(lane, ws.tb, ls, cnt, h0, col, tri, flag);
-                }
+                const int nu = put_entry(nxt, lane, ws.tb);
+                nxt = fetch_entry(b + 32 + lane, pe, col, twin, hrem);   // in flight meanwhile
+                int nc;
+                const int units = compact_warp(lane, nu, ws.tb, nc);
+                if (MERGE) merge_streams(lane, 0, 32, ws.tb, ids, hv, cnt, col, flag);
+                else if (use_bitmap) walk_units<lookup_bitmap, true, 32>(lane, ws.tb, nc, 0, units, lb, cnt, h0, col, tri, flag);
+                else walk_units<lookup_sorted, true, 32>(lane, ws.tb, nc, 0, units, ls, cnt, h0, col, tri, flag);
                 __syncwarp();
                 close_stream(lane, ws.tb, tri, flag, tv);
                 __syncwarp();
@@ -522,11 +488,11 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
 
 // ------------------------------------------------------------- CTA items
 // One CTA per item; the 8 warps share the staged N_H(v).  The item's head
-// entries are taken in rounds of 256 (a stream table); the round's vector
-// chunks are split evenly over the warps and each lane then reads the head
-// and tail ids of its own stream.
+// entries are taken in rounds of 256 (a stream table, the next round's
+// entries loaded while this one streams); the round's units are split
+// evenly over the warps.
 template <int LOOK, bool MERGE>
-__global__ void __launch_bounds__(TC_CTA_THREADS)
+__global__ void __launch_bounds__(TC_CTA_THREADS, TC_CTA_MIN_BLOCKS)
 k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
             const int64_t* __restrict__ hstart, const int64_t* __restrict__ twin,
             const int32_t* __restrict__ hrem, const int32_t* __restrict__ it_v,
@@ -550,6 +516,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         if (it >= n_items) break;
         const int32_t v = it_v[it];
         const int64_t pb = it_pb[it], pe = it_pe[it];
+        entry nxt = fetch_entry(pb + t, pe, col, twin, hrem);
         const int64_t h0 = hstart[v], h1 = row_ptr[v + 1];
         const int hv = (int)(h1 - h0);
         uint32_t* cnt = nullptr;
@@ -572,11 +539,10 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         }
         ull tv = 0;
         for (int64_t r0 = pb; r0 < pe; r0 += 256) {
-            int64_t va, vb;
-            load_entry(r0 + t, pe, t, col, twin, hrem, tb, va, vb);
-            // compact the streams with vector work over the round: warp
-            // scans of the unit counts, then the warp totals
-            const int nu = (int)((vb - va) >> 2);
+            const int nu = put_entry(nxt, t, tb);
+            nxt = fetch_entry(r0 + 256 + t, pe, col, twin, hrem);   // in flight meanwhile
+            // compact the non-empty streams of the round: warp scans of the
+            // unit counts, then the warp totals
             const unsigned nz = __ballot_sync(FULL, nu > 0);
             int incl = nu;
 #pragma unroll
@@ -608,16 +574,12 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
                 merge_streams(lane, 32 * warp, 32 * warp + 32, tb, ls.ids, hv, cnt, col, flag);
             } else {
                 const int ub = (int)(((int64_t)U * warp) >> 3), ue = (int)(((int64_t)U * (warp + 1)) >> 3);
-                if (LOOK == L_BITMAP) {
+                if (LOOK == L_BITMAP)
                     walk_units<lookup_bitmap, true, 256>(lane, tb, NC, ub, ue, lb, cnt, h0, col, tri, flag);
-                    stream_scalars<lookup_bitmap, true>(t, tb, lb, cnt, h0, col, tri, flag);
-                } else if (LOOK == L_SORTED) {
+                else if (LOOK == L_SORTED)
                     walk_units<lookup_sorted, true, 256>(lane, tb, NC, ub, ue, ls, cnt, h0, col, tri, flag);
-                    stream_scalars<lookup_sorted, true>(t, tb, ls, cnt, h0, col, tri, flag);
-                } else {
+                else
                     walk_units<lookup_global, false, 256>(lane, tb, NC, ub, ue, lg, nullptr, h0, col, tri, flag);
-                    stream_scalars<lookup_global, false>(t, tb, lg, nullptr, h0, col, tri, flag);
-                }
             }
             __syncthreads();   // every unit of the round is done
             close_stream(t, tb, tri, flag, tv);
