@@ -310,10 +310,10 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
     TC_TRY(dalloc((void**)&g->edge_v, (m + 1) * 4, s));
     TC_TRY(dalloc((void**)&g->perm, (n + 1) * 4, s));
     TC_TRY(dalloc((void**)&g->row_ptr, (n + 2) * 8, s));
-    // 8 ids of padding: the count step reads whole 16-byte units, and the
-    // last unit of the last row may extend past 2m
-    TC_TRY(dalloc((void**)&g->col, (e2 + 8) * 4, s));
-    TC_CUDA(cudaMemsetAsync(g->col + e2, 0xff, 8 * 4, s));
+    // 32 ids of padding: the count step reads whole groups of 16-byte
+    // units, and the last group of the last row may extend past 2m
+    TC_TRY(dalloc((void**)&g->col, (e2 + 32) * 4, s));
+    TC_CUDA(cudaMemsetAsync(g->col + e2, 0xff, 32 * 4, s));
     TC_TRY(dalloc((void**)&g->hstart, (n + 1) * 8, s));
     TC_TRY(dalloc((void**)&g->twin, (e2 + 1) * 8, s));
     TC_TRY(dalloc((void**)&g->hrem, (e2 + 1) * 4, s));

@@ -41,6 +41,9 @@ typedef unsigned long long ull;
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kCtaWarps = TC_CTA_THREADS / 32;
+#ifndef TC_CTA_MIN_BLOCKS
+#define TC_CTA_MIN_BLOCKS 4   // CTAs per SM the CTA-item kernels are compiled for
+#endif
 
 // Planner constants.
 constexpr int64_t kBitmapSmallSmem = 32 * 1024;   // dynamic smem of the small-bitmap CTA kernel (5 CTAs per SM)
@@ -55,20 +58,20 @@ enum { L_BITMAP = 0, L_SORTED = 1, L_GLOBAL = 2 };
 // ------------------------------------------------------------ lookups
 // N_H(v) as a bitmap over [base, base + nbits): bit (w - base) set iff
 // w ∈ N_H(v); rank[k] = set bits before word k (16 bits suffice since
-// |N_H(v)| <= sqrt(2m) < 2^16) gives w's staged index.
+// |N_H(v)| <= sqrt(2m) < 2^16) gives w's staged index.  Bit nbits is
+// always clear (a zero guard word follows the window), so an id outside the
+// window is clamped onto it and the test needs no branch.
 struct lookup_bitmap {
     const uint32_t* bits;
     const uint16_t* rank;
     int32_t base;
     int32_t nbits;
     __device__ __forceinline__ bool find(int32_t w, int& l) const {
-        const uint32_t off = (uint32_t)(w - base);
-        if (off >= (uint32_t)nbits) return false;
+        const uint32_t off = min((uint32_t)(w - base), (uint32_t)nbits);
         const uint32_t word = bits[off >> 5];
-        const uint32_t bit = 1u << (off & 31);
-        if (!(word & bit)) return false;
-        l = (int)rank[off >> 5] + __popc(word & (bit - 1));
-        return true;
+        const uint32_t below = word & ((1u << (off & 31)) - 1);
+        l = (int)rank[off >> 5] + __popc(below);
+        return (word >> (off & 31)) & 1u;
     }
 };
 
@@ -114,7 +117,7 @@ struct lookup_global {
 
 // Shared bytes of a bitmap staging: bits, 16-bit ranks, per-id counters.
 __host__ __device__ __forceinline__ int64_t bitmap_bytes(int64_t words, int64_t hv) {
-    return 4 * words + 2 * ((words + 1) & ~1ll) + 4 * hv;
+    return 4 * (words + 1) + 2 * ((words + 2) & ~1ll) + 4 * hv;   // + one zero guard word
 }
 
 __device__ __forceinline__ ull warp_sum(ull x) {
@@ -130,11 +133,11 @@ __device__ __forceinline__ lookup_bitmap build_bitmap(int t, int nt, uint8_t* re
                                                       uint32_t*& cnt, Barrier barrier,
                                                       uint32_t* scan_tmp, int lane, int warp, int nwarps) {
     const int words = (nbits + 31) >> 5;
-    uint32_t* bits = (uint32_t*)region;
-    uint16_t* rank = (uint16_t*)(bits + words);
-    cnt = (uint32_t*)(rank + ((words + 1) & ~1));
+    uint32_t* bits = (uint32_t*)region;                     // words + 1 (guard)
+    uint16_t* rank = (uint16_t*)(bits + words + 1);         // words + 1, padded to even
+    cnt = (uint32_t*)(rank + ((words + 2) & ~1));
     const int32_t base = v + 1;
-    for (int i = t; i < words; i += nt) bits[i] = 0;
+    for (int i = t; i <= words; i += nt) bits[i] = 0;
     for (int i = t; i < hv; i += nt) cnt[i] = 0;
     barrier();
     for (int i = t; i < hv; i += nt) {
@@ -165,24 +168,25 @@ __device__ __forceinline__ lookup_bitmap build_bitmap(int t, int nt, uint8_t* re
         rank[i] = (uint16_t)run;
         run += __popc(bits[i]);
     }
+    if (t == nt - 1) rank[words] = (uint16_t)(before + incl);   // guard word
     barrier();
     return lookup_bitmap{bits, rank, base, nbits};
 }
 
 // ------------------------------------------------------------ streams
 // A batch of head entries (lower neighbours u of the item's middle vertex
-// v) is a table of streams: stream i is col[p0, p0 + len), the part of
-// N_H(u) above v (p0 = twin(u,v) + 1).  Every stream is read as whole
-// 4-aligned units [p0 & ~3, (p0 + len + 3) & ~3) with 16-byte vector loads;
-// the ids of its first and last unit that lie outside it are masked.
+// v) gives one stream per non-empty entry: col[p0, p0 + len), the part of
+// N_H(u) above v (p0 = twin(u,v) + 1).  A stream is read as whole groups of
+// G 4-aligned units starting at p0 & ~3 (16-byte vector loads, G per lane);
+// ids outside [p0, p0 + len) are masked.  The table holds the non-empty
+// streams of the batch, compacted.
 template <int N>
 struct stream_table {
     int64_t va[N];        // first unit of the stream (4-aligned position)
     int32_t fl[N];        // (len << 2) | (p0 - va)
     int32_t u[N];
     uint32_t hits[N];
-    int32_t upre[N + 1];  // non-empty streams, compacted: units before each
-    int32_t cidx[N];      // ... and the table slot of each
+    int32_t gpre[N + 1];  // groups before each stream
 };
 
 // A head entry as loaded from global memory.
@@ -204,41 +208,47 @@ __device__ __forceinline__ entry fetch_entry(int64_t p, int64_t pe, const int32_
     return e;
 }
 
-// Puts an entry into slot i; returns its number of 4-id units.
-template <int N>
-__device__ __forceinline__ int put_entry(const entry& e, int i, stream_table<N>& tb) {
-    int nu = 0, fl = 0;
-    int64_t va = 0;
-    if (e.r > 0) {
-        const int64_t p0 = e.t + 1;
-        va = p0 & ~3ll;
-        nu = (int)((((p0 + e.r + 3) & ~3ll) - va) >> 2);
-        fl = (e.r << 2) | (int)(p0 - va);
-    }
-    tb.va[i] = va;
-    tb.fl[i] = fl;
-    tb.u[i] = e.u;
-    tb.hits[i] = 0;
-    return nu;
+// Number of G-unit groups of an entry's stream (0 if empty).
+template <int G>
+__device__ __forceinline__ int entry_groups(const entry& e) {
+    if (e.r == 0) return 0;
+    const int64_t p0 = e.t + 1;
+    const int units = (int)((((p0 + e.r + 3) & ~3ll) - (p0 & ~3ll)) >> 2);
+    return (units + G - 1) / G;
 }
 
-// Credits the hits of stream i to △(u) and flags the edge (u, v).
 template <int N>
-__device__ __forceinline__ void close_stream(int i, stream_table<N>& tb, ull* __restrict__ tri,
+__device__ __forceinline__ void put_stream(const entry& e, int k, int gpre, stream_table<N>& tb) {
+    const int64_t p0 = e.t + 1;
+    const int64_t va = p0 & ~3ll;
+    tb.va[k] = va;
+    tb.fl[k] = (e.r << 2) | (int)(p0 - va);
+    tb.u[k] = e.u;
+    tb.hits[k] = 0;
+    tb.gpre[k] = gpre;
+}
+
+// Credits the hits of stream k to △(u) and flags the edge (u, v).
+template <int N>
+__device__ __forceinline__ void close_stream(int k, stream_table<N>& tb, ull* __restrict__ tri,
                                              uint8_t* __restrict__ flag, ull& tv) {
-    const uint32_t c = tb.hits[i];
+    const uint32_t c = tb.hits[k];
     if (c) {
-        atomicAdd(&tri[tb.u[i]], (ull)c);
-        flag[tb.va[i] + (tb.fl[i] & 3) - 1] = 1;   // twin(u, v): the canonical entry of (u, v)
+        atomicAdd(&tri[tb.u[k]], (ull)c);
+        flag[tb.va[k] + (tb.fl[k] & 3) - 1] = 1;   // twin(u, v): the canonical entry of (u, v)
         tv += c;
     }
 }
 
-// The ids of one unit at pos whose offsets off+k (k = 0..3) from the
-// stream start lie in [0, len): look each up; on a hit count the triangle
-// (u, v, w) at the staged index; set the unit's hit flags with one 32-bit
-// OR (the unit's 4 flag bytes form one aligned word, and an OR never clears
-// a flag another thread set).  Returns the number of hits.
+__device__ __forceinline__ int4 load4(const int32_t* __restrict__ col, int64_t pos) {
+    return __ldg(reinterpret_cast<const int4*>(col + pos));
+}
+
+// One unit (4 ids at the 4-aligned position pos, the first at offset off
+// from the stream start): ids with offset in [0, len) are looked up; a hit
+// counts the triangle (u, v, w) at the staged index, and the unit's hit
+// flags are set with one 32-bit OR (its 4 flag bytes form one aligned word,
+// and an OR never clears a flag another thread set).  Returns the hits.
 template <class LK, bool CNT>
 __device__ __forceinline__ uint32_t visit_unit(const LK& lk, int4 w, int64_t pos, int off, int len,
                                                uint32_t* cnt, int64_t h0, ull* __restrict__ tri,
@@ -248,7 +258,8 @@ __device__ __forceinline__ uint32_t visit_unit(const LK& lk, int4 w, int64_t pos
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         int l = 0;
-        if ((unsigned)(off + k) < (unsigned)len && lk.find(ws[k], l)) {
+        const bool hit = lk.find(ws[k], l) && (unsigned)(off + k) < (unsigned)len;
+        if (hit) {
             if (CNT) {
                 atomicAdd(&cnt[l], 1u);
             } else {
@@ -262,96 +273,68 @@ __device__ __forceinline__ uint32_t visit_unit(const LK& lk, int4 w, int64_t pos
     return (uint32_t)__popc(bits);
 }
 
-__device__ __forceinline__ int4 load4(const int32_t* __restrict__ col, int64_t pos) {
-    return __ldg(reinterpret_cast<const int4*>(col + pos));
-}
-
-#ifndef TC_UNITS_IN_FLIGHT
-#define TC_UNITS_IN_FLIGHT 4
-#endif
-#ifndef TC_CTA_MIN_BLOCKS
-#define TC_CTA_MIN_BLOCKS 4
-#endif
-constexpr int kVec = TC_UNITS_IN_FLIGHT;   // 16-byte loads in flight per lane
-
-// Walks the units [ub, ue) of the concatenated streams of a table (its nc
-// compacted non-empty streams), lane-consecutively.  The stream of each
-// lane is found from the starts of the next 32 streams that fall inside
-// the current 32-unit window (one warp OR-reduction); s_base is the
-// stream holding the unit before the window.
-template <class LK, bool CNT, int N>
-__device__ __forceinline__ void walk_units(int lane, stream_table<N>& tb, int nc, int ub, int ue,
-                                           const LK& lk, uint32_t* cnt, int64_t h0,
-                                           const int32_t* __restrict__ col, ull* __restrict__ tri,
-                                           uint8_t* __restrict__ flag) {
-    if (ub >= ue) return;
+// Walks the groups [gb, ge) of the concatenated streams of a table (nc
+// streams), one group of G units per lane per window.  The stream of each
+// lane is found from the starts of the next 32 streams that fall inside the
+// current 32-group window (one warp OR-reduction); s_base is the stream
+// holding the group before the window.
+template <class LK, bool CNT, int N, int G>
+__device__ __forceinline__ void walk_groups(int lane, stream_table<N>& tb, int nc, int gb, int ge,
+                                            const LK& lk, uint32_t* cnt, int64_t h0,
+                                            const int32_t* __restrict__ col, ull* __restrict__ tri,
+                                            uint8_t* __restrict__ flag) {
+    if (gb >= ge) return;
     int s_base = -1;
-    if (ub > 0) {   // last stream starting at or before unit ub - 1
+    if (gb > 0) {   // last stream starting at or before group gb - 1
         s_base = 0;
 #pragma unroll
         for (int step = N / 2; step; step >>= 1)
-            if (s_base + step < nc && tb.upre[s_base + step] <= ub - 1) s_base += step;
+            if (s_base + step < nc && tb.gpre[s_base + step] <= gb - 1) s_base += step;
     }
     const unsigned le = FULL >> (31 - lane);
-    for (int F = ub; F < ue; F += 32 * kVec) {
-        int64_t pos[kVec];
-        int slot[kVec], off[kVec], len[kVec];
-        unsigned smask[kVec];
-        bool ok[kVec];
-        int4 w[kVec];
+    for (int F = gb; F < ge; F += 32) {
+        const int cand = s_base + 1 + lane;
+        const int st = cand < nc ? tb.gpre[cand] : 0x7fffffff;
+        const unsigned rel = (unsigned)(st - F);
+        const unsigned smask = __reduce_or_sync(FULL, rel < 32u ? (1u << rel) : 0u);
+        const int my = s_base + __popc(smask & le);
+        s_base += __popc(smask);
+        const int q = F + lane;
+        uint32_t h = 0;
+        if (q < ge) {
+            const int go = q - tb.gpre[my];
+            const int f = tb.fl[my];
+            const int64_t pos = tb.va[my] + (int64_t)(4 * G) * go;
+            const int off0 = 4 * G * go - (f & 3), len = f >> 2;
+            int4 w[G];
 #pragma unroll
-        for (int j = 0; j < kVec; ++j) {
-            const int Fj = F + 32 * j;
-            const int cand = s_base + 1 + lane;
-            const int st = cand < nc ? tb.upre[cand] : 0x7fffffff;
-            const unsigned rel = (unsigned)(st - Fj);
-            smask[j] = __reduce_or_sync(FULL, rel < 32u ? (1u << rel) : 0u);
-            const int my = s_base + __popc(smask[j] & le);
-            s_base += __popc(smask[j]);
-            const int q = Fj + lane;
-            ok[j] = q < ue;
-            slot[j] = 0;
-            pos[j] = 0;
-            off[j] = 0;
-            len[j] = 0;
-            if (ok[j]) {
-                slot[j] = tb.cidx[my];
-                const int uo = q - tb.upre[my];
-                const int f = tb.fl[slot[j]];
-                pos[j] = tb.va[slot[j]] + 4ll * uo;
-                off[j] = 4 * uo - (f & 3);
-                len[j] = f >> 2;
-            }
+            for (int j = 0; j < G; ++j) w[j] = load4(col, pos + 4 * j);
+#pragma unroll
+            for (int j = 0; j < G; ++j)
+                h += visit_unit<LK, CNT>(lk, w[j], pos + 4 * j, off0 + 4 * j, len, cnt, h0, tri, flag);
         }
-#pragma unroll
-        for (int j = 0; j < kVec; ++j) w[j] = ok[j] ? load4(col, pos[j]) : make_int4(-1, -1, -1, -1);
-#pragma unroll
-        for (int j = 0; j < kVec; ++j) {
-            const uint32_t h = ok[j] ? visit_unit<LK, CNT>(lk, w[j], pos[j], off[j], len[j], cnt, h0, tri, flag) : 0u;
-            if ((smask[j] & ~1u) == 0) {
-                // the whole window lies in one stream
-                const uint32_t sum = __reduce_add_sync(FULL, h);
-                if (lane == 0 && sum) atomicAdd(&tb.hits[slot[j]], sum);
-            } else if (h) {
-                atomicAdd(&tb.hits[slot[j]], h);
-            }
+        if ((smask & ~1u) == 0) {
+            // the whole window lies in one stream
+            const uint32_t sum = __reduce_add_sync(FULL, h);
+            if (lane == 0 && sum) atomicAdd(&tb.hits[my], sum);
+        } else if (h) {
+            atomicAdd(&tb.hits[my], h);
         }
     }
 }
 
 // Merge-path intersection of the staged A = N_H(v) (shared, ascending)
-// with each stream B in turn.  The 32 lanes split the merge path of A and
-// B into equal diagonals; on ties the A element is consumed first, and a
-// common id is counted when its A element is consumed while the current B
-// element equals it.
+// with streams [k0, k1) of a table in turn.  The 32 lanes split the merge
+// path of A and B into equal diagonals; on ties the A element is consumed
+// first, and a common id is counted when its A element is consumed while
+// the current B element equals it.
 template <int N>
-__device__ __forceinline__ void merge_streams(int lane, int i0, int i1, stream_table<N>& tb,
+__device__ __forceinline__ void merge_streams(int lane, int k0, int k1, stream_table<N>& tb,
                                               const int32_t* A, int na, uint32_t* cnt,
                                               const int32_t* __restrict__ col,
                                               uint8_t* __restrict__ flag) {
-    for (int i = i0; i < i1; ++i) {
+    for (int i = k0; i < k1; ++i) {
         const int nb = tb.fl[i] >> 2;
-        if (nb == 0) continue;
         const int64_t p0 = tb.va[i] + (tb.fl[i] & 3);
         const int32_t* B = col + p0;
         const int L = na + nb;
@@ -395,25 +378,32 @@ __device__ __forceinline__ bool warp_bitmap_fits(int64_t words, int64_t hv) {
     return hv < 65536 && bitmap_bytes(words, hv) <= kWarpSmem;
 }
 
-// Compacts the non-empty streams of a warp's 32-entry table; returns the
-// total number of units.
-__device__ __forceinline__ int compact_warp(int lane, int nu, stream_table<32>& tb, int& nc) {
-    const unsigned nz = __ballot_sync(FULL, nu > 0);
-    int incl = nu;
+// Compacts a warp's 32 entries into its stream table; returns the total
+// number of groups and the number of streams in nc.
+template <int G>
+__device__ __forceinline__ int compact_warp(int lane, const entry& e, stream_table<32>& tb, int& nc) {
+    const int ng = entry_groups<G>(e);
+    const unsigned nz = __ballot_sync(FULL, ng > 0);
+    int incl = ng;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const int x = __shfl_up_sync(FULL, incl, d);
         if (lane >= d) incl += x;
     }
-    if (nu > 0) {
-        const int k = __popc(nz & ((1u << lane) - 1));
-        tb.upre[k] = incl - nu;
-        tb.cidx[k] = lane;
-    }
+    if (ng > 0) put_stream(e, __popc(nz & ((1u << lane) - 1)), incl - ng, tb);
     nc = __popc(nz);
     __syncwarp();
     return __shfl_sync(FULL, incl, 31);
 }
+
+#ifndef TC_WARP_G
+#define TC_WARP_G 2
+#endif
+#ifndef TC_CTA_G
+#define TC_CTA_G 4
+#endif
+constexpr int kWarpG = TC_WARP_G;   // units (4 ids) per lane per window, warp items
+constexpr int kCtaG = TC_CTA_G;     // units per lane per window, CTA items
 
 template <bool MERGE>
 __global__ void __launch_bounds__(TC_CTA_THREADS, 3)
@@ -459,15 +449,15 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
             const lookup_sorted ls{ids, hv};
             ull tv = 0;
             for (int64_t b = pb; b < pe; b += 32) {
-                const int nu = put_entry(nxt, lane, ws.tb);
+                const entry cur = nxt;
                 nxt = fetch_entry(b + 32 + lane, pe, col, twin, hrem);   // in flight meanwhile
                 int nc;
-                const int units = compact_warp(lane, nu, ws.tb, nc);
-                if (MERGE) merge_streams(lane, 0, 32, ws.tb, ids, hv, cnt, col, flag);
-                else if (use_bitmap) walk_units<lookup_bitmap, true, 32>(lane, ws.tb, nc, 0, units, lb, cnt, h0, col, tri, flag);
-                else walk_units<lookup_sorted, true, 32>(lane, ws.tb, nc, 0, units, ls, cnt, h0, col, tri, flag);
+                const int groups = compact_warp<kWarpG>(lane, cur, ws.tb, nc);
+                if (MERGE) merge_streams(lane, 0, nc, ws.tb, ids, hv, cnt, col, flag);
+                else if (use_bitmap) walk_groups<lookup_bitmap, true, 32, kWarpG>(lane, ws.tb, nc, 0, groups, lb, cnt, h0, col, tri, flag);
+                else walk_groups<lookup_sorted, true, 32, kWarpG>(lane, ws.tb, nc, 0, groups, ls, cnt, h0, col, tri, flag);
                 __syncwarp();
-                close_stream(lane, ws.tb, tri, flag, tv);
+                if (lane < nc) close_stream(lane, ws.tb, tri, flag, tv);
                 __syncwarp();
             }
             for (int i = lane; i < hv; i += 32) {
@@ -539,12 +529,13 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         }
         ull tv = 0;
         for (int64_t r0 = pb; r0 < pe; r0 += 256) {
-            const int nu = put_entry(nxt, t, tb);
+            const entry cur = nxt;
             nxt = fetch_entry(r0 + 256 + t, pe, col, twin, hrem);   // in flight meanwhile
-            // compact the non-empty streams of the round: warp scans of the
-            // unit counts, then the warp totals
-            const unsigned nz = __ballot_sync(FULL, nu > 0);
-            int incl = nu;
+            // compact the round's non-empty streams: warp scans of the group
+            // counts, then the warp totals
+            const int ng = entry_groups<kCtaG>(cur);
+            const unsigned nz = __ballot_sync(FULL, ng > 0);
+            int incl = ng;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const int x = __shfl_up_sync(FULL, incl, d);
@@ -555,34 +546,30 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
                 s_cnt[warp] = __popc(nz);
             }
             __syncthreads();
-            int before_u = 0, before_c = 0, U = 0, NC = 0;
+            int before_g = 0, before_c = 0, GT = 0, NC = 0;
+#pragma unroll
             for (int k = 0; k < kCtaWarps; ++k) {
-                if (k < warp) {
-                    before_u += (int)s_scan[k];
-                    before_c += s_cnt[k];
-                }
-                U += (int)s_scan[k];
-                NC += s_cnt[k];
+                const int sg = (int)s_scan[k], sc = s_cnt[k];
+                before_g += k < warp ? sg : 0;
+                before_c += k < warp ? sc : 0;
+                GT += sg;
+                NC += sc;
             }
-            if (nu > 0) {
-                const int k = before_c + __popc(nz & ((1u << lane) - 1));
-                tb.upre[k] = before_u + incl - nu;
-                tb.cidx[k] = t;
-            }
+            if (ng > 0) put_stream(cur, before_c + __popc(nz & ((1u << lane) - 1)), before_g + incl - ng, tb);
             __syncthreads();
             if (MERGE) {
-                merge_streams(lane, 32 * warp, 32 * warp + 32, tb, ls.ids, hv, cnt, col, flag);
+                merge_streams(lane, (NC * warp) >> 3, (NC * (warp + 1)) >> 3, tb, ls.ids, hv, cnt, col, flag);
             } else {
-                const int ub = (int)(((int64_t)U * warp) >> 3), ue = (int)(((int64_t)U * (warp + 1)) >> 3);
+                const int gb = (int)(((int64_t)GT * warp) >> 3), ge = (int)(((int64_t)GT * (warp + 1)) >> 3);
                 if (LOOK == L_BITMAP)
-                    walk_units<lookup_bitmap, true, 256>(lane, tb, NC, ub, ue, lb, cnt, h0, col, tri, flag);
+                    walk_groups<lookup_bitmap, true, 256, kCtaG>(lane, tb, NC, gb, ge, lb, cnt, h0, col, tri, flag);
                 else if (LOOK == L_SORTED)
-                    walk_units<lookup_sorted, true, 256>(lane, tb, NC, ub, ue, ls, cnt, h0, col, tri, flag);
+                    walk_groups<lookup_sorted, true, 256, kCtaG>(lane, tb, NC, gb, ge, ls, cnt, h0, col, tri, flag);
                 else
-                    walk_units<lookup_global, false, 256>(lane, tb, NC, ub, ue, lg, nullptr, h0, col, tri, flag);
+                    walk_groups<lookup_global, false, 256, kCtaG>(lane, tb, NC, gb, ge, lg, nullptr, h0, col, tri, flag);
             }
-            __syncthreads();   // every unit of the round is done
-            close_stream(t, tb, tri, flag, tv);
+            __syncthreads();   // every group of the round is done
+            if (t < NC) close_stream(t, tb, tri, flag, tv);
             __syncthreads();   // before the table is overwritten
         }
         tv = warp_sum(tv);
