@@ -146,6 +146,19 @@ __global__ void k_twin(const uint64_t* __restrict__ keys, const uint32_t* __rest
     }
 }
 
+// First ranks whose degree exceeds 32 and 4096 (degrees ascend with rank).
+__global__ void k_bands(const int64_t* __restrict__ row_ptr, int64_t n, int64_t* __restrict__ band) {
+    const int64_t lim[2] = {32, 4096};
+    for (int k = 0; k < 2; ++k) {
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t mid = lo + ((hi - lo) >> 1);
+            if (row_ptr[mid + 1] - row_ptr[mid] > lim[k]) hi = mid; else lo = mid + 1;
+        }
+        band[k] = lo;
+    }
+}
+
 // ------------------------------------------------------------ row work
 struct row_stats {
     unsigned long long sum_h2, wedges, sum_dh, max_h, max_d;
@@ -422,8 +435,16 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
                                                             dst_stats);
         TC_LAUNCH_CHECK();
     }
+    int64_t* d_band = nullptr;
+    TC_TRY(sc.get(&d_band, 2));
+    {
+        launch_scope ls("build_bands", s);
+        k_bands<<<1, 1, 0, s>>>(g->row_ptr, n, d_band);
+        TC_LAUNCH_CHECK();
+    }
     row_stats hst{};
     TC_CUDA(cudaMemcpyAsync(&hst, dst_stats, sizeof(row_stats), cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaMemcpyAsync(g->band, d_band, sizeof(g->band), cudaMemcpyDeviceToHost, s));
     TC_CUDA(cudaStreamSynchronize(s));
     tc_graph_stats& S = g->stats;
     S.n = n;

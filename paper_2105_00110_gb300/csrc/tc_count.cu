@@ -609,6 +609,7 @@ __global__ void k_classify(const int64_t* __restrict__ row_ptr, const int64_t* _
                            const int32_t* __restrict__ col, const int64_t* __restrict__ work,
                            int64_t n, int strategy, int64_t* __restrict__ cnt,
                            int8_t* __restrict__ cls, class_acc* __restrict__ acc) {
+    ull loc[4][TC_NUM_CLS] = {};   // per-thread sums, reduced per warp at the end
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = n - 1 - i;
@@ -645,14 +646,30 @@ __global__ void k_classify(const int64_t* __restrict__ row_ptr, const int64_t* _
             chunks = (W + chunk - 1) / chunk;
             if (chunks > lv) chunks = lv;
             if (chunks < 1) chunks = 1;
-            atomicAdd(&acc->items[c], (ull)chunks);
-            atomicAdd(&acc->staged[c], (ull)hv);
-            atomicAdd(&acc->head[c], (ull)lv);
-            atomicAdd(&acc->wedges[c], (ull)W);
+#pragma unroll
+            for (int cc = 0; cc < TC_NUM_CLS; ++cc)   // static indices keep loc in registers
+                if (cc == c) {
+                    loc[0][cc] += (ull)chunks;
+                    loc[1][cc] += (ull)hv;
+                    loc[2][cc] += (ull)lv;
+                    loc[3][cc] += (ull)W;
+                }
         }
         cls[i] = (int8_t)c;
         for (int k = 0; k < TC_NUM_CLS; ++k) cnt[k * (n + 1) + i] = (k == c) ? chunks : 0;
     }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < TC_NUM_CLS; ++c) {
+            ull x = loc[a][c];
+            for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0 && x) {
+                ull* dst = a == 0 ? acc->items : a == 1 ? acc->staged : a == 2 ? acc->head : acc->wedges;
+                atomicAdd(&dst[c], x);
+            }
+        }
 }
 
 __global__ void k_emit(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,

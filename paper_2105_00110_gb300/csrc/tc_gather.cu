@@ -8,6 +8,8 @@
 // and divided once by 3△(G).  u ∈ N△(v) is the edge flag of (v, u): for a
 // tail entry of row v (u above v) the flag sits at the entry itself, for a
 // head entry (u below v) at its twin, the canonical entry in row u.
+#include <algorithm>
+
 #include "tc_internal.cuh"
 
 namespace tcx {
@@ -64,34 +66,78 @@ __device__ __forceinline__ ull warp_sum(ull x) {
     return x;
 }
 
-// One warp per row of the rank-space CSR.
-__global__ void __launch_bounds__(256)
-k_gather(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
-         const int32_t* __restrict__ col, const int64_t* __restrict__ twin,
-         const uint8_t* __restrict__ flag, const ull* __restrict__ tri,
-         const int32_t* __restrict__ perm, int64_t n, ull den, ull* __restrict__ numer_rank,
-         ull* __restrict__ numer_out, double* __restrict__ tc_out) {
+// numer(r) = △(r) + Σ_{p ∈ row r} (u ∈ N△(r) ? 1 : 3)·△(col[p]).  The flag
+// of a tail entry sits at the entry, that of a head entry at its twin.
+// Rows are in rank (= degree) order, so three contiguous rank bands get
+// one thread, one warp and one CTA per row.
+__device__ __forceinline__ void finish_row(int64_t r, ull acc, const int32_t* __restrict__ perm, ull den,
+                                           ull* __restrict__ numer_rank, ull* __restrict__ numer_out,
+                                           double* __restrict__ tc_out) {
+    numer_rank[r] = acc;
+    const int32_t v = perm[r];
+    if (numer_out) numer_out[v] = acc;
+    if (tc_out) tc_out[v] = div_rn(acc, den);
+}
+
+struct gather_args {
+    const int64_t* row_ptr;
+    const int64_t* hstart;
+    const int32_t* col;
+    const int64_t* twin;
+    const uint8_t* flag;
+    const ull* tri;
+    const int32_t* perm;
+    ull den;
+    ull* numer_rank;
+    ull* numer_out;
+    double* tc_out;
+};
+
+// one thread per row, rows [r0, r1)
+__global__ void __launch_bounds__(256) k_gather_thread(gather_args a, int64_t r0, int64_t r1) {
+    for (int64_t r = r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < r1;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = a.row_ptr[r], h = a.hstart[r], e = a.row_ptr[r + 1];
+        ull acc = a.tri[r];
+        for (int64_t p = b; p < h; ++p) acc += (a.flag[a.twin[p]] ? 1ull : 3ull) * a.tri[a.col[p]];
+        for (int64_t p = h; p < e; ++p) acc += (a.flag[p] ? 1ull : 3ull) * a.tri[a.col[p]];
+        finish_row(r, acc, a.perm, a.den, a.numer_rank, a.numer_out, a.tc_out);
+    }
+}
+
+// one warp per row, rows [r0, r1)
+__global__ void __launch_bounds__(256) k_gather_warp(gather_args a, int64_t r0, int64_t r1) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
-        const int64_t b = row_ptr[r], h = hstart[r], e = row_ptr[r + 1];
+    for (int64_t r = r0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); r < r1; r += warps) {
+        const int64_t b = a.row_ptr[r], h = a.hstart[r], e = a.row_ptr[r + 1];
         ull acc = 0;
-        for (int64_t p = b + lane; p < h; p += 32) {
-            ull w = flag[twin[p]] ? 1ull : 3ull;
-            acc += w * tri[col[p]];
-        }
-        for (int64_t p = h + lane; p < e; p += 32) {
-            ull w = flag[p] ? 1ull : 3ull;
-            acc += w * tri[col[p]];
-        }
+        for (int64_t p = b + lane; p < h; p += 32) acc += (a.flag[a.twin[p]] ? 1ull : 3ull) * a.tri[a.col[p]];
+        for (int64_t p = h + lane; p < e; p += 32) acc += (a.flag[p] ? 1ull : 3ull) * a.tri[a.col[p]];
         acc = warp_sum(acc);
-        if (lane == 0) {
-            acc += tri[r];
-            numer_rank[r] = acc;
-            const int32_t v = perm[r];
-            if (numer_out) numer_out[v] = acc;
-            if (tc_out) tc_out[v] = div_rn(acc, den);
+        if (lane == 0) finish_row(r, acc + a.tri[r], a.perm, a.den, a.numer_rank, a.numer_out, a.tc_out);
+    }
+}
+
+// one CTA per row, rows [r0, r1)
+__global__ void __launch_bounds__(1024) k_gather_cta(gather_args a, int64_t r0, int64_t r1) {
+    __shared__ ull part[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
+        const int64_t b = a.row_ptr[r], h = a.hstart[r], e = a.row_ptr[r + 1];
+        ull acc = 0;
+        for (int64_t p = b + threadIdx.x; p < h; p += blockDim.x)
+            acc += (a.flag[a.twin[p]] ? 1ull : 3ull) * a.tri[a.col[p]];
+        for (int64_t p = h + threadIdx.x; p < e; p += blockDim.x) acc += (a.flag[p] ? 1ull : 3ull) * a.tri[a.col[p]];
+        acc = warp_sum(acc);
+        if (lane == 0) part[warp] = acc;
+        __syncthreads();
+        if (warp == 0) {
+            ull x = lane < (int)(blockDim.x >> 5) ? part[lane] : 0ull;
+            x = warp_sum(x);
+            if (lane == 0) finish_row(r, x + a.tri[r], a.perm, a.den, a.numer_rank, a.numer_out, a.tc_out);
         }
+        __syncthreads();
     }
 }
 
@@ -127,12 +173,25 @@ inline int blocks_for(int64_t items, int threads) {
 tc_status run_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, cudaStream_t s) {
     const int64_t n = g->n;
     if (n == 0) return TC_OK;
-    const ull den = 3ull * (ull)g->total;
-    launch_scope ls("gather", s);
-    k_gather<<<blocks_for(n * 32, 256), 256, 0, s>>>(g->row_ptr, g->hstart, g->col, g->twin,
-                                                      g->flag, g->tri, g->perm, n, den, g->numer,
-                                                      (ull*)d_numer, d_tc);
-    TC_LAUNCH_CHECK();
+    gather_args a{g->row_ptr, g->hstart, g->col, g->twin, g->flag, g->tri, g->perm,
+                  3ull * (ull)g->total, g->numer, (ull*)d_numer, d_tc};
+    const int64_t r1 = g->band[0], r2 = g->band[1];   // degree <= 32 | <= 4096 | larger
+    if (r1 > 0) {
+        launch_scope ls("gather_thread", s);
+        k_gather_thread<<<blocks_for(r1, 256), 256, 0, s>>>(a, 0, r1);
+        TC_LAUNCH_CHECK();
+    }
+    if (r2 > r1) {
+        launch_scope ls("gather_warp", s);
+        k_gather_warp<<<blocks_for((r2 - r1) * 32, 256), 256, 0, s>>>(a, r1, r2);
+        TC_LAUNCH_CHECK();
+    }
+    if (n > r2) {
+        launch_scope ls("gather_cta", s);
+        const int64_t rows = n - r2;
+        k_gather_cta<<<(int)std::min<int64_t>(rows, (int64_t)sm_count() * 2), 1024, 0, s>>>(a, r2, n);
+        TC_LAUNCH_CHECK();
+    }
     return TC_OK;
 }
 

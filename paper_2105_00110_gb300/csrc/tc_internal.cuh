@@ -65,6 +65,7 @@ struct tc_graph {
     int32_t* hrem = nullptr;
     int64_t* edge_tail = nullptr;
     int64_t* work = nullptr;             // [n] W(v) = Σ_{u ∈ N_L(v)} hrem(u, v)
+    int64_t band[2] = {0, 0};            // first rank of degree > 32, of degree > 4096
     tc_plan plan;
     // workspace of tc_count / tc_centrality
     unsigned long long* tri = nullptr;   // [n], rank space
