@@ -88,61 +88,48 @@ __global__ void k_rank_apply(const uint64_t* __restrict__ sorted, int64_t n, int
     if (blockIdx.x == 0 && threadIdx.x == 0) degr[n] = 0;
 }
 
-__global__ void k_directed_keys(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
-                                const int32_t* __restrict__ rank, int64_t m, int bits,
-                                uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// Every undirected edge once in rank space: key (lo, hi) with lo < hi the
+// ranks of its ends, value its canonical id; d_H(lo) counted.
+__global__ void k_edge_rank_keys(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                                 const int32_t* __restrict__ rank, int64_t m, int bits,
+                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                 int32_t* __restrict__ dh) {
     GRID_STRIDE(e, m) {
-        uint64_t ru = (uint64_t)rank[eu[e]], rv = (uint64_t)rank[ev[e]];
-        keys[2 * e] = (ru << bits) | rv;
-        keys[2 * e + 1] = (rv << bits) | ru;
-        vals[2 * e] = (uint32_t)e;
-        vals[2 * e + 1] = (uint32_t)e;
+        const uint64_t ru = (uint64_t)rank[eu[e]], rv = (uint64_t)rank[ev[e]];
+        const uint64_t lo = ru < rv ? ru : rv, hi = ru < rv ? rv : ru;
+        keys[e] = (lo << bits) | hi;
+        vals[e] = (uint32_t)e;
+        atomicAdd(&dh[lo], 1);
     }
 }
 
-// col, and the tail position of every canonical edge.
-__global__ void k_csr_cols(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                           int64_t e2, int bits, int32_t* __restrict__ col,
-                           int64_t* __restrict__ edge_tail) {
+// Row split: the last d_H(r) entries of row r hold N_H(r).
+__global__ void k_hstart(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ dh, int64_t n,
+                         int64_t* __restrict__ hstart) {
+    GRID_STRIDE(r, n) hstart[r] = row_ptr[r + 1] - dh[r];
+}
+
+// Writes both entries of every edge.  The edges arrive sorted by (lo, hi),
+// so the tail entry (row lo, N_H(lo) ascending) of the i-th edge is at
+// hstart[lo] + (i - hptr[lo]); the head entry (row hi, N_L(hi) in any
+// order) takes the next free slot of row hi's head, and records twin and
+// hrem: the tail position and |{w ∈ N_H(lo) : w > hi}|.
+__global__ void k_scatter(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t m,
+                          int bits, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
+                          const int64_t* __restrict__ hptr, int32_t* __restrict__ hcur,
+                          int32_t* __restrict__ col, int64_t* __restrict__ twin, int32_t* __restrict__ hrem,
+                          int64_t* __restrict__ edge_tail) {
     const uint64_t mask = (1ull << bits) - 1;
-    GRID_STRIDE(p, e2) {
-        uint64_t k = keys[p];
-        uint64_t row = k >> bits, c = k & mask;
-        col[p] = (int32_t)c;
-        if (c > row) edge_tail[vals[p]] = p;
-    }
-}
-
-// hstart[r]: first entry of row r with a label above r.
-__global__ void k_hstart(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                         int64_t n, int64_t* __restrict__ hstart) {
-    GRID_STRIDE(r, n) {
-        int64_t lo = row_ptr[r], hi = row_ptr[r + 1];
-        while (lo < hi) {
-            int64_t mid = lo + ((hi - lo) >> 1);
-            if ((int64_t)col[mid] <= r) lo = mid + 1; else hi = mid;
-        }
-        hstart[r] = lo;
-    }
-}
-
-// twin / hrem of head entries (col < row).
-__global__ void k_twin(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                       const int64_t* __restrict__ edge_tail, const int64_t* __restrict__ row_ptr,
-                       int64_t e2, int bits, int64_t* __restrict__ twin,
-                       int32_t* __restrict__ hrem) {
-    const uint64_t mask = (1ull << bits) - 1;
-    GRID_STRIDE(p, e2) {
-        uint64_t k = keys[p];
-        uint64_t row = k >> bits, c = k & mask;
-        if (c < row) {
-            int64_t t = edge_tail[vals[p]];
-            twin[p] = t;
-            hrem[p] = (int32_t)(row_ptr[c + 1] - t - 1);
-        } else {
-            twin[p] = -1;
-            hrem[p] = 0;
-        }
+    GRID_STRIDE(i, m) {
+        const uint64_t k = keys[i];
+        const int64_t lo = (int64_t)(k >> bits), hi = (int64_t)(k & mask);
+        const int64_t tail = hstart[lo] + (i - hptr[lo]);
+        col[tail] = (int32_t)hi;
+        edge_tail[vals[i]] = tail;
+        const int64_t head = row_ptr[hi] + atomicAdd(&hcur[hi], 1);
+        col[head] = (int32_t)lo;
+        twin[head] = tail;
+        hrem[head] = (int32_t)(row_ptr[lo + 1] - tail - 1);
     }
 }
 
@@ -378,49 +365,58 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
         TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, bytes, degr, g->row_ptr, n + 1, s));
     }
 
-    // ---- 4. rank-space symmetric CSR
-    uint64_t* dkeys = nullptr;
-    uint32_t* dvals = nullptr;
+    // ---- 4. rank-space CSR: the m edges sorted once by (lo, hi) give every
+    // N_H(r) in order; the heads N_L(r) need no order
     if (m > 0) {
-        uint64_t *da = nullptr, *db = nullptr;
+        uint64_t *ka2 = nullptr, *kb2p = nullptr;
         uint32_t *va = nullptr, *vb = nullptr;
-        TC_TRY(sc.get(&da, e2));
-        TC_TRY(sc.get(&db, e2));
-        TC_TRY(sc.get(&va, e2));
-        TC_TRY(sc.get(&vb, e2));
+        int32_t *dh = nullptr, *hcur = nullptr;
+        int64_t* hptr = nullptr;
+        TC_TRY(sc.get(&ka2, m));
+        TC_TRY(sc.get(&kb2p, m));
+        TC_TRY(sc.get(&va, m));
+        TC_TRY(sc.get(&vb, m));
+        TC_TRY(sc.get(&dh, n + 1));
+        TC_TRY(sc.get(&hcur, n + 1));
+        TC_TRY(sc.get(&hptr, n + 1));
+        TC_CUDA(cudaMemsetAsync(dh, 0, (n + 1) * 4, s));
+        TC_CUDA(cudaMemsetAsync(hcur, 0, (n + 1) * 4, s));
         {
-            launch_scope ls("build_directed_keys", s);
-            k_directed_keys<<<grid_for(m), kThreads, 0, s>>>(g->edge_u, g->edge_v, rank, m, bits, da, va);
+            launch_scope ls("build_edge_rank_keys", s);
+            k_edge_rank_keys<<<grid_for(m), kThreads, 0, s>>>(g->edge_u, g->edge_v, rank, m, bits, ka2, va, dh);
             TC_LAUNCH_CHECK();
         }
-        cub::DoubleBuffer<uint64_t> kb2(da, db);
+        cub::DoubleBuffer<uint64_t> kb2(ka2, kb2p);
         cub::DoubleBuffer<uint32_t> vb2(va, vb);
         size_t bytes = 0;
-        TC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb2, vb2, e2, 0, 2 * bits, s));
+        TC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb2, vb2, m, 0, 2 * bits, s));
+        size_t sbytes = 0;
+        TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, sbytes, dh, hptr, n + 1, s));
         uint8_t* tmp = nullptr;
-        TC_TRY(sc.get(&tmp, bytes));
+        TC_TRY(sc.get(&tmp, std::max(bytes, sbytes)));
         {
-            launch_scope ls("build_sort_directed", s);
-            TC_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb2, vb2, e2, 0, 2 * bits, s));
+            launch_scope ls("build_sort_edges", s);
+            TC_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb2, vb2, m, 0, 2 * bits, s));
         }
-        dkeys = kb2.Current();
-        dvals = vb2.Current();
         {
-            launch_scope ls("build_csr_cols", s);
-            k_csr_cols<<<grid_for(e2), kThreads, 0, s>>>(dkeys, dvals, e2, bits, g->col, g->edge_tail);
+            launch_scope ls("build_hptr", s);
+            TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, sbytes, dh, hptr, n + 1, s));
+        }
+        {
+            launch_scope ls("build_hstart", s);
+            k_hstart<<<grid_for(n), kThreads, 0, s>>>(g->row_ptr, dh, n, g->hstart);
             TC_LAUNCH_CHECK();
         }
-    }
-    if (n > 0) {
-        launch_scope ls("build_hstart", s);
-        k_hstart<<<grid_for(n), kThreads, 0, s>>>(g->row_ptr, g->col, n, g->hstart);
-        TC_LAUNCH_CHECK();
-    }
-    if (m > 0) {
-        launch_scope ls("build_twin", s);
-        k_twin<<<grid_for(e2), kThreads, 0, s>>>(dkeys, dvals, g->edge_tail, g->row_ptr, e2, bits,
-                                                 g->twin, g->hrem);
-        TC_LAUNCH_CHECK();
+        {
+            launch_scope ls("build_scatter", s);
+            k_scatter<<<grid_for(m), kThreads, 0, s>>>(kb2.Current(), vb2.Current(), m, bits, g->row_ptr,
+                                                        g->hstart, hptr, hcur, g->col, g->twin, g->hrem,
+                                                        g->edge_tail);
+            TC_LAUNCH_CHECK();
+        }
+    } else if (n > 0) {
+        // no edges: every row is empty
+        TC_CUDA(cudaMemsetAsync(g->hstart, 0, n * 8, s));
     }
 
     // ---- 6. per-row work, statistics and the count-step plan
