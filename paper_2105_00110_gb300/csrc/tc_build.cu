@@ -64,7 +64,9 @@ __global__ void k_edges_degrees(const uint64_t* __restrict__ ukeys, int64_t m, i
         int32_t u = (int32_t)(k >> bits), v = (int32_t)(k & mask);
         eu[e] = u;
         ev[e] = v;
-        atomicAdd(&deg[u], 1);
+        // edges are sorted by u: lanes with the same u add their count once
+        const unsigned same = __match_any_sync(__activemask(), u);
+        if ((threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&deg[u], __popc(same));
         atomicAdd(&deg[v], 1);
     }
 }
@@ -112,12 +114,12 @@ __global__ void k_hstart(const int64_t* __restrict__ row_ptr, const int32_t* __r
 // Writes both entries of every edge.  The edges arrive sorted by (lo, hi),
 // so the tail entry (row lo, N_H(lo) ascending) of the i-th edge is at
 // hstart[lo] + (i - hptr[lo]); the head entry (row hi, N_L(hi) in any
-// order) takes the next free slot of row hi's head, and records twin and
-// hrem: the tail position and |{w ∈ N_H(lo) : w > hi}|.
+// order) takes the next free slot of row hi's head as the record
+// {lo, |{w ∈ N_H(lo) : w > hi}|, tail position}.
 __global__ void k_scatter(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t m,
                           int bits, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
                           const int64_t* __restrict__ hptr, int32_t* __restrict__ hcur,
-                          int32_t* __restrict__ col, int64_t* __restrict__ twin, int32_t* __restrict__ hrem,
+                          int32_t* __restrict__ col, tc_head* __restrict__ head,
                           int64_t* __restrict__ edge_tail) {
     const uint64_t mask = (1ull << bits) - 1;
     GRID_STRIDE(i, m) {
@@ -126,10 +128,12 @@ __global__ void k_scatter(const uint64_t* __restrict__ keys, const uint32_t* __r
         const int64_t tail = hstart[lo] + (i - hptr[lo]);
         col[tail] = (int32_t)hi;
         edge_tail[vals[i]] = tail;
-        const int64_t head = row_ptr[hi] + atomicAdd(&hcur[hi], 1);
-        col[head] = (int32_t)lo;
-        twin[head] = tail;
-        hrem[head] = (int32_t)(row_ptr[lo + 1] - tail - 1);
+        const int64_t hp = row_ptr[hi] + atomicAdd(&hcur[hi], 1);
+        tc_head rec;
+        rec.u = (int32_t)lo;
+        rec.hrem = (int32_t)(row_ptr[lo + 1] - tail - 1);
+        rec.twin = tail;
+        head[hp] = rec;   // one 16-byte store
     }
 }
 
@@ -154,7 +158,7 @@ struct row_stats {
 // One warp per row: W(v) = Σ_{u ∈ N_L(v)} hrem(u, v), the number of ids the
 // count step streams for middle vertex v; plus shape statistics.
 __global__ void k_row_work(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
-                           const int32_t* __restrict__ hrem, int64_t n, int64_t* __restrict__ work,
+                           const tc_head* __restrict__ head, int64_t n, int64_t* __restrict__ work,
                            row_stats* __restrict__ st) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -162,7 +166,7 @@ __global__ void k_row_work(const int64_t* __restrict__ row_ptr, const int64_t* _
     for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
         const int64_t b = row_ptr[r], h = hstart[r], e = row_ptr[r + 1];
         unsigned long long w = 0;
-        for (int64_t p = b + lane; p < h; p += 32) w += (unsigned long long)hrem[p];
+        for (int64_t p = b + lane; p < h; p += 32) w += (unsigned long long)head[p].hrem;
         for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
         if (lane == 0) {
             const unsigned long long hv = (unsigned long long)(e - h), d = (unsigned long long)(e - b);
@@ -222,8 +226,8 @@ tc_status sort_keys(scratch& sc, cub::DoubleBuffer<T>& buf, int64_t count, int e
 
 void free_graph_memory(tc_graph* g) {
     cudaStream_t s = g->stream;
-    void* ptrs[] = {g->edge_u, g->edge_v, g->perm, g->row_ptr, g->col, g->hstart, g->twin,
-                    g->hrem, g->edge_tail, g->work, g->tri, g->flag, g->numer, g->counters};
+    void* ptrs[] = {g->edge_u, g->edge_v, g->perm, g->row_ptr, g->col, g->hstart, g->head,
+                    g->edge_tail, g->work, g->tri, g->flag, g->numer, g->counters};
     for (void* q : ptrs) dfree(q, s);
     free_plan(g->plan, s);
 }
@@ -315,8 +319,7 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
     TC_TRY(dalloc((void**)&g->col, (e2 + 32) * 4, s));
     TC_CUDA(cudaMemsetAsync(g->col + e2, 0xff, 32 * 4, s));
     TC_TRY(dalloc((void**)&g->hstart, (n + 1) * 8, s));
-    TC_TRY(dalloc((void**)&g->twin, (e2 + 1) * 8, s));
-    TC_TRY(dalloc((void**)&g->hrem, (e2 + 1) * 4, s));
+    TC_TRY(dalloc((void**)&g->head, (e2 + 1) * sizeof(tc_head), s));
     TC_TRY(dalloc((void**)&g->edge_tail, (m + 1) * 8, s));
     TC_TRY(dalloc((void**)&g->tri, (n + 1) * 8, s));
     TC_TRY(dalloc((void**)&g->numer, (n + 1) * 8, s));
@@ -410,7 +413,7 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
         {
             launch_scope ls("build_scatter", s);
             k_scatter<<<grid_for(m), kThreads, 0, s>>>(kb2.Current(), vb2.Current(), m, bits, g->row_ptr,
-                                                        g->hstart, hptr, hcur, g->col, g->twin, g->hrem,
+                                                        g->hstart, hptr, hcur, g->col, g->head,
                                                         g->edge_tail);
             TC_LAUNCH_CHECK();
         }
@@ -427,7 +430,7 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
     if (n > 0) {
         launch_scope ls("build_row_work", s);
         int blocks = (int)std::min<int64_t>((n * 32 + kThreads - 1) / kThreads, (int64_t)sm_count() * 16);
-        k_row_work<<<std::max(blocks, 1), kThreads, 0, s>>>(g->row_ptr, g->hstart, g->hrem, n, g->work,
+        k_row_work<<<std::max(blocks, 1), kThreads, 0, s>>>(g->row_ptr, g->hstart, g->head, n, g->work,
                                                             dst_stats);
         TC_LAUNCH_CHECK();
     }

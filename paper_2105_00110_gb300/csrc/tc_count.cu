@@ -196,14 +196,13 @@ struct entry {
     int64_t t;     // twin(u, v)
 };
 
-__device__ __forceinline__ entry fetch_entry(int64_t p, int64_t pe, const int32_t* __restrict__ col,
-                                             const int64_t* __restrict__ twin,
-                                             const int32_t* __restrict__ hrem) {
+__device__ __forceinline__ entry fetch_entry(int64_t p, int64_t pe, const tc_head* __restrict__ head) {
     entry e{0, 0, 0};
     if (p < pe) {
-        e.r = hrem[p];
-        e.t = twin[p];
-        e.u = col[p];
+        const tc_head rec = head[p];   // one 16-byte load
+        e.r = rec.hrem;
+        e.t = rec.twin;
+        e.u = rec.u;
     }
     return e;
 }
@@ -408,8 +407,8 @@ constexpr int kCtaG = TC_CTA_G;     // units per lane per window, CTA items
 template <bool MERGE>
 __global__ void __launch_bounds__(TC_CTA_THREADS, 3)
 k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-             const int64_t* __restrict__ hstart, const int64_t* __restrict__ twin,
-             const int32_t* __restrict__ hrem, const int32_t* __restrict__ it_v,
+             const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
+             const int32_t* __restrict__ it_v,
              const int64_t* __restrict__ it_pb, const int64_t* __restrict__ it_pe,
              int64_t n_items, ull* __restrict__ cursor, int strategy, ull* __restrict__ tri,
              uint8_t* __restrict__ flag, ull* __restrict__ total) {
@@ -428,7 +427,7 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
         for (int64_t it = base; it < lim; ++it) {
             const int32_t v = it_v[it];
             const int64_t pb = it_pb[it], pe = it_pe[it];
-            entry nxt = fetch_entry(pb + lane, pe, col, twin, hrem);
+            entry nxt = fetch_entry(pb + lane, pe, head);
             const int64_t h0 = hstart[v], h1 = row_ptr[v + 1];
             const int hv = (int)(h1 - h0);
             const int32_t nbits = col[h1 - 1] - v;
@@ -450,7 +449,7 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
             ull tv = 0;
             for (int64_t b = pb; b < pe; b += 32) {
                 const entry cur = nxt;
-                nxt = fetch_entry(b + 32 + lane, pe, col, twin, hrem);   // in flight meanwhile
+                nxt = fetch_entry(b + 32 + lane, pe, head);   // in flight meanwhile
                 int nc;
                 const int groups = compact_warp<kWarpG>(lane, cur, ws.tb, nc);
                 if (MERGE) merge_streams(lane, 0, nc, ws.tb, ids, hv, cnt, col, flag);
@@ -484,8 +483,8 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
 template <int LOOK, bool MERGE>
 __global__ void __launch_bounds__(TC_CTA_THREADS, TC_CTA_MIN_BLOCKS)
 k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-            const int64_t* __restrict__ hstart, const int64_t* __restrict__ twin,
-            const int32_t* __restrict__ hrem, const int32_t* __restrict__ it_v,
+            const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
+            const int32_t* __restrict__ it_v,
             const int64_t* __restrict__ it_pb, const int64_t* __restrict__ it_pe,
             int64_t n_items, ull* __restrict__ cursor, int strategy, ull* __restrict__ tri,
             uint8_t* __restrict__ flag, ull* __restrict__ total) {
@@ -506,7 +505,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         if (it >= n_items) break;
         const int32_t v = it_v[it];
         const int64_t pb = it_pb[it], pe = it_pe[it];
-        entry nxt = fetch_entry(pb + t, pe, col, twin, hrem);
+        entry nxt = fetch_entry(pb + t, pe, head);
         const int64_t h0 = hstart[v], h1 = row_ptr[v + 1];
         const int hv = (int)(h1 - h0);
         uint32_t* cnt = nullptr;
@@ -530,7 +529,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         ull tv = 0;
         for (int64_t r0 = pb; r0 < pe; r0 += 256) {
             const entry cur = nxt;
-            nxt = fetch_entry(r0 + 256 + t, pe, col, twin, hrem);   // in flight meanwhile
+            nxt = fetch_entry(r0 + 256 + t, pe, head);   // in flight meanwhile
             // compact the round's non-empty streams: warp scans of the group
             // counts, then the warp totals
             const int ng = entry_groups<kCtaG>(cur);
@@ -711,7 +710,7 @@ tc_status launch_persistent(K kernel, const char* name, size_t smem, int64_t ite
     per_sm = std::max(per_sm, 1);
     int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, items);
     launch_scope ls(name, s);
-    kernel<<<(int)blocks, TC_CTA_THREADS, smem, s>>>(g->row_ptr, g->col, g->hstart, g->twin, g->hrem,
+    kernel<<<(int)blocks, TC_CTA_THREADS, smem, s>>>(g->row_ptr, g->col, g->hstart, g->head,
                                                      p.v[c], p.pb[c], p.pe[c], items, cursor,
                                                      g->strategy, g->tri, g->flag, g->counters);
     TC_LAUNCH_CHECK();

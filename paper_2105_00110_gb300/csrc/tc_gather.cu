@@ -66,8 +66,9 @@ __device__ __forceinline__ ull warp_sum(ull x) {
     return x;
 }
 
-// numer(r) = △(r) + Σ_{p ∈ row r} (u ∈ N△(r) ? 1 : 3)·△(col[p]).  The flag
-// of a tail entry sits at the entry, that of a head entry at its twin.
+// numer(r) = △(r) + Σ_{u ∈ N(r)} (u ∈ N△(r) ? 1 : 3)·△(u).  A tail entry
+// holds u in col and its flag in place; a head entry's record holds u and
+// the twin position where its flag sits.
 // Rows are in rank (= degree) order, so three contiguous rank bands get
 // one thread, one warp and one CTA per row.
 __device__ __forceinline__ void finish_row(int64_t r, ull acc, const int32_t* __restrict__ perm, ull den,
@@ -83,7 +84,7 @@ struct gather_args {
     const int64_t* row_ptr;
     const int64_t* hstart;
     const int32_t* col;
-    const int64_t* twin;
+    const tc_head* head;
     const uint8_t* flag;
     const ull* tri;
     const int32_t* perm;
@@ -99,7 +100,10 @@ __global__ void __launch_bounds__(256) k_gather_thread(gather_args a, int64_t r0
          r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = a.row_ptr[r], h = a.hstart[r], e = a.row_ptr[r + 1];
         ull acc = a.tri[r];
-        for (int64_t p = b; p < h; ++p) acc += (a.flag[a.twin[p]] ? 1ull : 3ull) * a.tri[a.col[p]];
+        for (int64_t p = b; p < h; ++p) {
+            const tc_head rec = a.head[p];
+            acc += (a.flag[rec.twin] ? 1ull : 3ull) * a.tri[rec.u];
+        }
         for (int64_t p = h; p < e; ++p) acc += (a.flag[p] ? 1ull : 3ull) * a.tri[a.col[p]];
         finish_row(r, acc, a.perm, a.den, a.numer_rank, a.numer_out, a.tc_out);
     }
@@ -112,7 +116,10 @@ __global__ void __launch_bounds__(256) k_gather_warp(gather_args a, int64_t r0, 
     for (int64_t r = r0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); r < r1; r += warps) {
         const int64_t b = a.row_ptr[r], h = a.hstart[r], e = a.row_ptr[r + 1];
         ull acc = 0;
-        for (int64_t p = b + lane; p < h; p += 32) acc += (a.flag[a.twin[p]] ? 1ull : 3ull) * a.tri[a.col[p]];
+        for (int64_t p = b + lane; p < h; p += 32) {
+            const tc_head rec = a.head[p];
+            acc += (a.flag[rec.twin] ? 1ull : 3ull) * a.tri[rec.u];
+        }
         for (int64_t p = h + lane; p < e; p += 32) acc += (a.flag[p] ? 1ull : 3ull) * a.tri[a.col[p]];
         acc = warp_sum(acc);
         if (lane == 0) finish_row(r, acc + a.tri[r], a.perm, a.den, a.numer_rank, a.numer_out, a.tc_out);
@@ -126,8 +133,10 @@ __global__ void __launch_bounds__(1024) k_gather_cta(gather_args a, int64_t r0, 
     for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
         const int64_t b = a.row_ptr[r], h = a.hstart[r], e = a.row_ptr[r + 1];
         ull acc = 0;
-        for (int64_t p = b + threadIdx.x; p < h; p += blockDim.x)
-            acc += (a.flag[a.twin[p]] ? 1ull : 3ull) * a.tri[a.col[p]];
+        for (int64_t p = b + threadIdx.x; p < h; p += blockDim.x) {
+            const tc_head rec = a.head[p];
+            acc += (a.flag[rec.twin] ? 1ull : 3ull) * a.tri[rec.u];
+        }
         for (int64_t p = h + threadIdx.x; p < e; p += blockDim.x) acc += (a.flag[p] ? 1ull : 3ull) * a.tri[a.col[p]];
         acc = warp_sum(acc);
         if (lane == 0) part[warp] = acc;
@@ -173,7 +182,7 @@ inline int blocks_for(int64_t items, int threads) {
 tc_status run_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, cudaStream_t s) {
     const int64_t n = g->n;
     if (n == 0) return TC_OK;
-    gather_args a{g->row_ptr, g->hstart, g->col, g->twin, g->flag, g->tri, g->perm,
+    gather_args a{g->row_ptr, g->hstart, g->col, g->head, g->flag, g->tri, g->perm,
                   3ull * (ull)g->total, g->numer, (ull*)d_numer, d_tc};
     const int64_t r1 = g->band[0], r2 = g->band[1];   // degree <= 32 | <= 4096 | larger
     if (r1 > 0) {

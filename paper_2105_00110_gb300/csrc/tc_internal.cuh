@@ -8,11 +8,13 @@
 //   col[2m]       int32   neighbour ranks, each row ascending, so row r is
 //                         [ N_L(r) | N_H(r) ] with the split at hstart[r]
 //   hstart[n]     int64   first position of N_H(r) in row r
-//   twin[2m]      int64   for a head entry p = (v, u), u < v: the position of
-//                         v inside N_H(u) (row u); unused for tail entries
-//   hrem[2m]      int32   for a head entry: |{w ∈ N_H(u) : w > v}|, the
-//                         length of the part of N_H(u) that can close a
-//                         triangle with the oriented edge u -> v
+//   head[2m]      16 B    for a head entry p = (v, u), u < v (row v's part
+//                         [row_ptr, hstart), in no particular order): the
+//                         record {u, hrem, twin}: twin = the position of v
+//                         inside N_H(u) (row u), hrem = |{w ∈ N_H(u) : w > v}|,
+//                         the part of N_H(u) that can close a triangle with
+//                         the oriented edge u -> v.  col[] is not written at
+//                         head positions; tail positions hold N_H(v) ascending
 //   edge_tail[m]  int64   canonical edge e -> its tail position in rank space
 //   perm[n]       int32   rank -> caller label
 //   edge_u/v[m]   int32   canonical undirected edges, caller labels, u < v,
@@ -39,6 +41,13 @@ enum tc_item_class {
     TC_NUM_CLS = 4
 };
 
+// A head entry (see the layout above).
+struct __align__(16) tc_head {
+    int32_t u;
+    int32_t hrem;
+    int64_t twin;
+};
+
 struct tc_plan {
     int strategy = -1;                 // strategy the plan was made for
     int64_t count[TC_NUM_CLS] = {};
@@ -61,8 +70,7 @@ struct tc_graph {
     int64_t* row_ptr = nullptr;
     int32_t* col = nullptr;
     int64_t* hstart = nullptr;
-    int64_t* twin = nullptr;
-    int32_t* hrem = nullptr;
+    tc_head* head = nullptr;
     int64_t* edge_tail = nullptr;
     int64_t* work = nullptr;             // [n] W(v) = Σ_{u ∈ N_L(v)} hrem(u, v)
     int64_t band[2] = {0, 0};            // first rank of degree > 32, of degree > 4096
