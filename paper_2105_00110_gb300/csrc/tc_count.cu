@@ -69,9 +69,9 @@ struct lookup_bitmap {
     __device__ __forceinline__ bool find(int32_t w, int& l) const {
         const uint32_t off = min((uint32_t)(w - base), (uint32_t)nbits);
         const uint32_t word = bits[off >> 5];
-        const uint32_t below = word & ((1u << (off & 31)) - 1);
-        l = (int)rank[off >> 5] + __popc(below);
-        return (word >> (off & 31)) & 1u;
+        if (!((word >> (off & 31)) & 1u)) return false;
+        l = (int)rank[off >> 5] + __popc(word & ((1u << (off & 31)) - 1));
+        return true;
     }
 };
 
@@ -176,17 +176,18 @@ __device__ __forceinline__ lookup_bitmap build_bitmap(int t, int nt, uint8_t* re
 // ------------------------------------------------------------ streams
 // A batch of head entries (lower neighbours u of the item's middle vertex
 // v) gives one stream per non-empty entry: col[p0, p0 + len), the part of
-// N_H(u) above v (p0 = twin(u,v) + 1).  A stream is read as whole groups of
-// G 4-aligned units starting at p0 & ~3 (16-byte vector loads, G per lane);
-// ids outside [p0, p0 + len) are masked.  The table holds the non-empty
-// streams of the batch, compacted.
+// N_H(u) above v (p0 = twin(u,v) + 1).  A stream is read in octets: 8 ids
+// at an 8-aligned position, one 32-byte load (one whole sector), starting
+// at p0 & ~7; a lane takes G consecutive octets per window, and ids outside
+// [p0, p0 + len) are masked.  The table holds the batch's non-empty
+// streams, compacted.
 template <int N>
 struct stream_table {
-    int64_t va[N];        // first unit of the stream (4-aligned position)
-    int32_t fl[N];        // (len << 2) | (p0 - va)
+    int64_t va[N];        // first octet of the stream (8-aligned position)
+    int32_t fl[N];        // (len << 3) | (p0 - va)
     int32_t u[N];
     uint32_t hits[N];
-    int32_t gpre[N + 1];  // groups before each stream
+    int32_t gpre[N + 1];  // groups of G octets before each stream
 };
 
 // A head entry as loaded from global memory.
@@ -207,21 +208,21 @@ __device__ __forceinline__ entry fetch_entry(int64_t p, int64_t pe, const tc_hea
     return e;
 }
 
-// Number of G-unit groups of an entry's stream (0 if empty).
+// Number of G-octet groups of an entry's stream (0 if empty).
 template <int G>
 __device__ __forceinline__ int entry_groups(const entry& e) {
     if (e.r == 0) return 0;
     const int64_t p0 = e.t + 1;
-    const int units = (int)((((p0 + e.r + 3) & ~3ll) - (p0 & ~3ll)) >> 2);
-    return (units + G - 1) / G;
+    const int octets = (int)((((p0 + e.r + 7) & ~7ll) - (p0 & ~7ll)) >> 3);
+    return (octets + G - 1) / G;
 }
 
 template <int N>
 __device__ __forceinline__ void put_stream(const entry& e, int k, int gpre, stream_table<N>& tb) {
     const int64_t p0 = e.t + 1;
-    const int64_t va = p0 & ~3ll;
+    const int64_t va = p0 & ~7ll;
     tb.va[k] = va;
-    tb.fl[k] = (e.r << 2) | (int)(p0 - va);
+    tb.fl[k] = (e.r << 3) | (int)(p0 - va);
     tb.u[k] = e.u;
     tb.hits[k] = 0;
     tb.gpre[k] = gpre;
@@ -234,46 +235,56 @@ __device__ __forceinline__ void close_stream(int k, stream_table<N>& tb, ull* __
     const uint32_t c = tb.hits[k];
     if (c) {
         atomicAdd(&tri[tb.u[k]], (ull)c);
-        flag[tb.va[k] + (tb.fl[k] & 3) - 1] = 1;   // twin(u, v): the canonical entry of (u, v)
+        flag[tb.va[k] + (tb.fl[k] & 7) - 1] = 1;   // twin(u, v): the canonical entry of (u, v)
         tv += c;
     }
 }
 
-__device__ __forceinline__ int4 load4(const int32_t* __restrict__ col, int64_t pos) {
-    return __ldg(reinterpret_cast<const int4*>(col + pos));
+// 8 ids from an 8-aligned position: one 256-bit read-only load.
+struct octet {
+    int32_t x[8];
+};
+__device__ __forceinline__ octet load8(const int32_t* __restrict__ col, int64_t pos) {
+    octet o;
+    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(o.x[0]), "=r"(o.x[1]), "=r"(o.x[2]), "=r"(o.x[3]), "=r"(o.x[4]), "=r"(o.x[5]),
+                   "=r"(o.x[6]), "=r"(o.x[7])
+                 : "l"(col + pos));
+    return o;
 }
 
-// One unit (4 ids at the 4-aligned position pos, the first at offset off
+// One octet (8 ids at the 8-aligned position pos, the first at offset off
 // from the stream start): ids with offset in [0, len) are looked up; a hit
-// counts the triangle (u, v, w) at the staged index, and the unit's hit
-// flags are set with one 32-bit OR (its 4 flag bytes form one aligned word,
-// and an OR never clears a flag another thread set).  Returns the hits.
+// counts the triangle (u, v, w) at the staged index, and the octet's hit
+// flags are set with one 64-bit OR (its 8 flag bytes form one aligned
+// word, and an OR never clears a flag another thread set).  Returns the
+// hits.
 template <class LK, bool CNT>
-__device__ __forceinline__ uint32_t visit_unit(const LK& lk, int4 w, int64_t pos, int off, int len,
-                                               uint32_t* cnt, int64_t h0, ull* __restrict__ tri,
-                                               uint8_t* __restrict__ flag) {
-    const int32_t ws[4] = {w.x, w.y, w.z, w.w};
-    uint32_t bits = 0;
+__device__ __forceinline__ uint32_t visit_octet(const LK& lk, const octet& o, int64_t pos, int off, int len,
+                                                uint32_t* cnt, int64_t h0, ull* __restrict__ tri,
+                                                uint8_t* __restrict__ flag) {
+    ull bits = 0;
+    uint32_t nh = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 8; ++k) {
         int l = 0;
-        const bool hit = lk.find(ws[k], l) && (unsigned)(off + k) < (unsigned)len;
-        if (hit) {
+        if ((unsigned)(off + k) < (unsigned)len && lk.find(o.x[k], l)) {
             if (CNT) {
                 atomicAdd(&cnt[l], 1u);
             } else {
-                atomicAdd(&tri[ws[k]], 1ull);
+                atomicAdd(&tri[o.x[k]], 1ull);
                 flag[h0 + l] = 1;
             }
-            bits |= 1u << (8 * k);
+            bits |= 1ull << (8 * k);
+            ++nh;
         }
     }
-    if (bits) atomicOr(reinterpret_cast<unsigned int*>(flag + pos), bits);
-    return (uint32_t)__popc(bits);
+    if (bits) atomicOr(reinterpret_cast<ull*>(flag + pos), bits);
+    return nh;
 }
 
 // Walks the groups [gb, ge) of the concatenated streams of a table (nc
-// streams), one group of G units per lane per window.  The stream of each
+// streams), one group of G octets per lane per window.  The stream of each
 // lane is found from the starts of the next 32 streams that fall inside the
 // current 32-group window (one warp OR-reduction); s_base is the stream
 // holding the group before the window.
@@ -303,14 +314,14 @@ __device__ __forceinline__ void walk_groups(int lane, stream_table<N>& tb, int n
         if (q < ge) {
             const int go = q - tb.gpre[my];
             const int f = tb.fl[my];
-            const int64_t pos = tb.va[my] + (int64_t)(4 * G) * go;
-            const int off0 = 4 * G * go - (f & 3), len = f >> 2;
-            int4 w[G];
+            const int64_t pos = tb.va[my] + (int64_t)(8 * G) * go;
+            const int off0 = 8 * G * go - (f & 7), len = f >> 3;
+            octet o[G];
 #pragma unroll
-            for (int j = 0; j < G; ++j) w[j] = load4(col, pos + 4 * j);
+            for (int j = 0; j < G; ++j) o[j] = load8(col, pos + 8 * j);
 #pragma unroll
             for (int j = 0; j < G; ++j)
-                h += visit_unit<LK, CNT>(lk, w[j], pos + 4 * j, off0 + 4 * j, len, cnt, h0, tri, flag);
+                h += visit_octet<LK, CNT>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, h0, tri, flag);
         }
         if ((smask & ~1u) == 0) {
             // the whole window lies in one stream
@@ -333,8 +344,8 @@ __device__ __forceinline__ void merge_streams(int lane, int k0, int k1, stream_t
                                               const int32_t* __restrict__ col,
                                               uint8_t* __restrict__ flag) {
     for (int i = k0; i < k1; ++i) {
-        const int nb = tb.fl[i] >> 2;
-        const int64_t p0 = tb.va[i] + (tb.fl[i] & 3);
+        const int nb = tb.fl[i] >> 3;
+        const int64_t p0 = tb.va[i] + (tb.fl[i] & 7);
         const int32_t* B = col + p0;
         const int L = na + nb;
         const int d0 = (int)(((int64_t)L * lane) >> 5), d1 = (int)(((int64_t)L * (lane + 1)) >> 5);
@@ -396,13 +407,13 @@ __device__ __forceinline__ int compact_warp(int lane, const entry& e, stream_tab
 }
 
 #ifndef TC_WARP_G
-#define TC_WARP_G 2
+#define TC_WARP_G 1
 #endif
 #ifndef TC_CTA_G
-#define TC_CTA_G 4
+#define TC_CTA_G 2
 #endif
-constexpr int kWarpG = TC_WARP_G;   // units (4 ids) per lane per window, warp items
-constexpr int kCtaG = TC_CTA_G;     // units per lane per window, CTA items
+constexpr int kWarpG = TC_WARP_G;   // octets (8 ids) per lane per window, warp items
+constexpr int kCtaG = TC_CTA_G;     // octets per lane per window, CTA items
 
 template <bool MERGE>
 __global__ void __launch_bounds__(TC_CTA_THREADS, 3)
