@@ -283,6 +283,41 @@ __device__ __forceinline__ uint32_t visit_octet(const LK& lk, const octet& o, in
     return nh;
 }
 
+// The bitmap form in explicit phases — the 8 word loads, the hit mask, the
+// rank loads of the hits, then the counter atomics — so that the loads of
+// an octet overlap instead of each waiting behind the previous id's atomic.
+template <>
+__device__ __forceinline__ uint32_t visit_octet<lookup_bitmap, true>(const lookup_bitmap& lk, const octet& o,
+                                                                    int64_t pos, int off, int len,
+                                                                    uint32_t* cnt, int64_t h0,
+                                                                    ull* __restrict__ tri,
+                                                                    uint8_t* __restrict__ flag) {
+    uint32_t word[8], boff[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        boff[k] = min((uint32_t)(o.x[k] - lk.base), (uint32_t)lk.nbits);
+        word[k] = lk.bits[boff[k] >> 5];
+    }
+    uint32_t hm = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        hm |= (((word[k] >> (boff[k] & 31)) & 1u) & ((unsigned)(off + k) < (unsigned)len ? 1u : 0u)) << k;
+    if (hm == 0) return 0;
+    int l[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        l[k] = (hm >> k) & 1u ? (int)lk.rank[boff[k] >> 5] + __popc(word[k] & ((1u << (boff[k] & 31)) - 1)) : 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if ((hm >> k) & 1u) atomicAdd(&cnt[l[k]], 1u);
+    // spread the 8 hit bits to the low bit of each byte
+    ull bits = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) bits |= (ull)((hm >> k) & 1u) << (8 * k);
+    atomicOr(reinterpret_cast<ull*>(flag + pos), bits);
+    return (uint32_t)__popc(hm);
+}
+
 // Walks the groups [gb, ge) of the concatenated streams of a table (nc
 // streams), one group of G octets per lane per window.  The stream of each
 // lane is found from the starts of the next 32 streams that fall inside the
