@@ -451,7 +451,7 @@ constexpr int kWarpG = TC_WARP_G;   // octets (8 ids) per lane per window, warp 
 constexpr int kCtaG = TC_CTA_G;     // octets per lane per window, CTA items
 
 template <bool MERGE>
-__global__ void __launch_bounds__(TC_CTA_THREADS, 3)
+__global__ void __launch_bounds__(TC_CTA_THREADS, 4)
 k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
              const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
              const int32_t* __restrict__ it_v,
