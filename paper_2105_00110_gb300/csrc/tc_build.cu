@@ -323,7 +323,7 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
     TC_TRY(dalloc((void**)&g->edge_tail, (m + 1) * 8, s));
     TC_TRY(dalloc((void**)&g->tri, (n + 1) * 8, s));
     TC_TRY(dalloc((void**)&g->numer, (n + 1) * 8, s));
-    TC_TRY(dalloc((void**)&g->flag, e2 + 16, s));
+    TC_TRY(dalloc((void**)&g->flag, flag_words(e2) * 4, s));
     TC_TRY(dalloc((void**)&g->counters, 8 * 8, s));
 
     // ---- 3. degrees and the order π

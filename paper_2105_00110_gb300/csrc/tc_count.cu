@@ -231,11 +231,11 @@ __device__ __forceinline__ void put_stream(const entry& e, int k, int gpre, stre
 // Credits the hits of stream k to △(u) and flags the edge (u, v).
 template <int N>
 __device__ __forceinline__ void close_stream(int k, stream_table<N>& tb, ull* __restrict__ tri,
-                                             uint8_t* __restrict__ flag, ull& tv) {
+                                             uint32_t* __restrict__ flag, ull& tv) {
     const uint32_t c = tb.hits[k];
     if (c) {
         atomicAdd(&tri[tb.u[k]], (ull)c);
-        flag[tb.va[k] + (tb.fl[k] & 7) - 1] = 1;   // twin(u, v): the canonical entry of (u, v)
+        flag_set(flag, tb.va[k] + (tb.fl[k] & 7) - 1);   // twin(u, v): the canonical entry of (u, v)
         tv += c;
     }
 }
@@ -256,14 +256,13 @@ __device__ __forceinline__ octet load8(const int32_t* __restrict__ col, int64_t 
 // One octet (8 ids at the 8-aligned position pos, the first at offset off
 // from the stream start): ids with offset in [0, len) are looked up; a hit
 // counts the triangle (u, v, w) at the staged index, and the octet's hit
-// flags are set with one 64-bit OR (its 8 flag bytes form one aligned
-// word, and an OR never clears a flag another thread set).  Returns the
-// hits.
+// flags are set with one 32-bit OR (its 8 flag bits lie in one word, and an
+// OR never clears a flag another thread set).  Returns the hits.
 template <class LK, bool CNT>
 __device__ __forceinline__ uint32_t visit_octet(const LK& lk, const octet& o, int64_t pos, int off, int len,
                                                 uint32_t* cnt, int64_t h0, ull* __restrict__ tri,
-                                                uint8_t* __restrict__ flag) {
-    ull bits = 0;
+                                                uint32_t* __restrict__ flag) {
+    uint32_t bits = 0;
     uint32_t nh = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -273,13 +272,14 @@ __device__ __forceinline__ uint32_t visit_octet(const LK& lk, const octet& o, in
                 atomicAdd(&cnt[l], 1u);
             } else {
                 atomicAdd(&tri[o.x[k]], 1ull);
-                flag[h0 + l] = 1;
+                flag_set(flag, h0 + l);
             }
-            bits |= 1ull << (8 * k);
+            bits |= 1u << k;
             ++nh;
         }
     }
-    if (bits) atomicOr(reinterpret_cast<ull*>(flag + pos), bits);
+    // the octet's 8 flag bits lie in one 32-bit word (pos is 8-aligned)
+    if (bits) atomicOr(&flag[pos >> 5], (uint32_t)bits << (pos & 31));
     return nh;
 }
 
@@ -291,7 +291,7 @@ __device__ __forceinline__ uint32_t visit_octet<lookup_bitmap, true>(const looku
                                                                     int64_t pos, int off, int len,
                                                                     uint32_t* cnt, int64_t h0,
                                                                     ull* __restrict__ tri,
-                                                                    uint8_t* __restrict__ flag) {
+                                                                    uint32_t* __restrict__ flag) {
     uint32_t word[8], boff[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -310,11 +310,8 @@ __device__ __forceinline__ uint32_t visit_octet<lookup_bitmap, true>(const looku
 #pragma unroll
     for (int k = 0; k < 8; ++k)
         if ((hm >> k) & 1u) atomicAdd(&cnt[l[k]], 1u);
-    // spread the 8 hit bits to the low bit of each byte
-    ull bits = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) bits |= (ull)((hm >> k) & 1u) << (8 * k);
-    atomicOr(reinterpret_cast<ull*>(flag + pos), bits);
+    // the octet's 8 flag bits lie in one 32-bit word (pos is 8-aligned)
+    atomicOr(&flag[pos >> 5], hm << (pos & 31));
     return (uint32_t)__popc(hm);
 }
 
@@ -327,7 +324,7 @@ template <class LK, bool CNT, int N, int G>
 __device__ __forceinline__ void walk_groups(int lane, stream_table<N>& tb, int nc, int gb, int ge,
                                             const LK& lk, uint32_t* cnt, int64_t h0,
                                             const int32_t* __restrict__ col, ull* __restrict__ tri,
-                                            uint8_t* __restrict__ flag) {
+                                            uint32_t* __restrict__ flag) {
     if (gb >= ge) return;
     int s_base = -1;
     if (gb > 0) {   // last stream starting at or before group gb - 1
@@ -377,7 +374,7 @@ template <int N>
 __device__ __forceinline__ void merge_streams(int lane, int k0, int k1, stream_table<N>& tb,
                                               const int32_t* A, int na, uint32_t* cnt,
                                               const int32_t* __restrict__ col,
-                                              uint8_t* __restrict__ flag) {
+                                              uint32_t* __restrict__ flag) {
     for (int i = k0; i < k1; ++i) {
         const int nb = tb.fl[i] >> 3;
         const int64_t p0 = tb.va[i] + (tb.fl[i] & 7);
@@ -395,7 +392,7 @@ __device__ __forceinline__ void merge_streams(int lane, int k0, int k1, stream_t
             if (ia < na && (jb >= nb || A[ia] <= __ldg(B + jb))) {
                 if (jb < nb && __ldg(B + jb) == A[ia]) {
                     atomicAdd(&cnt[ia], 1u);
-                    flag[p0 + jb] = 1;
+                    flag_set(flag, p0 + jb);
                     ++found;
                 }
                 ++ia;
@@ -457,7 +454,7 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
              const int32_t* __restrict__ it_v,
              const int64_t* __restrict__ it_pb, const int64_t* __restrict__ it_pe,
              int64_t n_items, ull* __restrict__ cursor, int strategy, ull* __restrict__ tri,
-             uint8_t* __restrict__ flag, ull* __restrict__ total) {
+             uint32_t* __restrict__ flag, ull* __restrict__ total) {
     __shared__ __align__(16) warp_smem sm[kCtaWarps];
     const int lane = threadIdx.x & 31;
     warp_smem& ws = sm[threadIdx.x >> 5];
@@ -509,7 +506,7 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
                 const uint32_t c = cnt[i];
                 if (c) {
                     atomicAdd(&tri[col[h0 + i]], (ull)c);
-                    flag[h0 + i] = 1;
+                    flag_set(flag, h0 + i);
                 }
             }
             tv = warp_sum(tv);
@@ -533,7 +530,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             const int32_t* __restrict__ it_v,
             const int64_t* __restrict__ it_pb, const int64_t* __restrict__ it_pe,
             int64_t n_items, ull* __restrict__ cursor, int strategy, ull* __restrict__ tri,
-            uint8_t* __restrict__ flag, ull* __restrict__ total) {
+            uint32_t* __restrict__ flag, ull* __restrict__ total) {
     extern __shared__ __align__(16) uint8_t dyn[];
     __shared__ __align__(16) stream_table<256> tb;
     __shared__ int64_t s_item;
@@ -625,7 +622,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
                 const uint32_t c = cnt[i];
                 if (c) {
                     atomicAdd(&tri[col[h0 + i]], (ull)c);
-                    flag[h0 + i] = 1;
+                    flag_set(flag, h0 + i);
                 }
             }
         }
@@ -866,7 +863,7 @@ tc_status run_count(tc_graph* g, cudaStream_t s) {
     const int64_t n = g->n, e2 = 2 * g->m;
     if (g->plan.strategy != g->strategy) TC_TRY(make_plan(g, g->strategy, s));
     TC_CUDA(cudaMemsetAsync(g->tri, 0, (n + 1) * 8, s));
-    TC_CUDA(cudaMemsetAsync(g->flag, 0, e2 + 16, s));
+    TC_CUDA(cudaMemsetAsync(g->flag, 0, flag_words(e2) * 4, s));
     TC_CUDA(cudaMemsetAsync(g->counters, 0, 8 * 8, s));
     const tc_plan& p = g->plan;
     ull* cur = g->counters + 1;

@@ -85,7 +85,7 @@ struct gather_args {
     const int64_t* hstart;
     const int32_t* col;
     const tc_head* head;
-    const uint8_t* flag;
+    const uint32_t* flag;
     const ull* tri;
     const int32_t* perm;
     ull den;
@@ -102,9 +102,9 @@ __global__ void __launch_bounds__(256) k_gather_thread(gather_args a, int64_t r0
         ull acc = a.tri[r];
         for (int64_t p = b; p < h; ++p) {
             const tc_head rec = a.head[p];
-            acc += (a.flag[rec.twin] ? 1ull : 3ull) * a.tri[rec.u];
+            acc += (flag_get(a.flag, rec.twin) ? 1ull : 3ull) * a.tri[rec.u];
         }
-        for (int64_t p = h; p < e; ++p) acc += (a.flag[p] ? 1ull : 3ull) * a.tri[a.col[p]];
+        for (int64_t p = h; p < e; ++p) acc += (flag_get(a.flag, p) ? 1ull : 3ull) * a.tri[a.col[p]];
         finish_row(r, acc, a.perm, a.den, a.numer_rank, a.numer_out, a.tc_out);
     }
 }
@@ -118,9 +118,9 @@ __global__ void __launch_bounds__(256) k_gather_warp(gather_args a, int64_t r0, 
         ull acc = 0;
         for (int64_t p = b + lane; p < h; p += 32) {
             const tc_head rec = a.head[p];
-            acc += (a.flag[rec.twin] ? 1ull : 3ull) * a.tri[rec.u];
+            acc += (flag_get(a.flag, rec.twin) ? 1ull : 3ull) * a.tri[rec.u];
         }
-        for (int64_t p = h + lane; p < e; p += 32) acc += (a.flag[p] ? 1ull : 3ull) * a.tri[a.col[p]];
+        for (int64_t p = h + lane; p < e; p += 32) acc += (flag_get(a.flag, p) ? 1ull : 3ull) * a.tri[a.col[p]];
         acc = warp_sum(acc);
         if (lane == 0) finish_row(r, acc + a.tri[r], a.perm, a.den, a.numer_rank, a.numer_out, a.tc_out);
     }
@@ -135,9 +135,9 @@ __global__ void __launch_bounds__(1024) k_gather_cta(gather_args a, int64_t r0, 
         ull acc = 0;
         for (int64_t p = b + threadIdx.x; p < h; p += blockDim.x) {
             const tc_head rec = a.head[p];
-            acc += (a.flag[rec.twin] ? 1ull : 3ull) * a.tri[rec.u];
+            acc += (flag_get(a.flag, rec.twin) ? 1ull : 3ull) * a.tri[rec.u];
         }
-        for (int64_t p = h + threadIdx.x; p < e; p += blockDim.x) acc += (a.flag[p] ? 1ull : 3ull) * a.tri[a.col[p]];
+        for (int64_t p = h + threadIdx.x; p < e; p += blockDim.x) acc += (flag_get(a.flag, p) ? 1ull : 3ull) * a.tri[a.col[p]];
         acc = warp_sum(acc);
         if (lane == 0) part[warp] = acc;
         __syncthreads();
@@ -163,11 +163,11 @@ __global__ void k_export_tri(const ull* __restrict__ tri, const int32_t* __restr
         out[perm[r]] = tri[r];
 }
 
-__global__ void k_export_flags(const uint8_t* __restrict__ flag, const int64_t* __restrict__ edge_tail,
+__global__ void k_export_flags(const uint32_t* __restrict__ flag, const int64_t* __restrict__ edge_tail,
                                int64_t m, uint8_t* __restrict__ out) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x)
-        out[e] = flag[edge_tail[e]];
+        out[e] = flag_get(flag, edge_tail[e]) ? 1 : 0;
 }
 
 inline int blocks_for(int64_t items, int threads) {

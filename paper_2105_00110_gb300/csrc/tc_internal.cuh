@@ -16,6 +16,9 @@
 //                         the oriented edge u -> v.  col[] is not written at
 //                         head positions; tail positions hold N_H(v) ascending
 //   edge_tail[m]  int64   canonical edge e -> its tail position in rank space
+//   flag[2m/32]   uint32  one bit per CSR position: the in-a-triangle flag of
+//                         each edge, on its tail entry (65 MB at m = 2.6e8,
+//                         small enough to stay in L2 while the count runs)
 //   perm[n]       int32   rank -> caller label
 //   edge_u/v[m]   int32   canonical undirected edges, caller labels, u < v,
 //                         sorted by (u, v)
@@ -77,7 +80,7 @@ struct tc_graph {
     tc_plan plan;
     // workspace of tc_count / tc_centrality
     unsigned long long* tri = nullptr;   // [n], rank space
-    uint8_t* flag = nullptr;             // [2m], meaningful on tail entries
+    uint32_t* flag = nullptr;            // one bit per CSR position (2m bits), set on tail entries
     unsigned long long* numer = nullptr; // [n], rank space
     unsigned long long* counters = nullptr;  // [8]: 0 total, 1 warp cursor, 2 cta cursor
     int counted = 0;
@@ -87,6 +90,15 @@ struct tc_graph {
 };
 
 // ---------------------------------------------------------------- helpers
+// Edge flags, one bit per CSR position.
+__device__ __forceinline__ void flag_set(uint32_t* __restrict__ fb, int64_t p) {
+    atomicOr(&fb[p >> 5], 1u << (p & 31));
+}
+__device__ __forceinline__ bool flag_get(const uint32_t* __restrict__ fb, int64_t p) {
+    return (fb[p >> 5] >> (p & 31)) & 1u;
+}
+inline int64_t flag_words(int64_t e2) { return (e2 >> 5) + 4; }
+
 namespace tcx {
 
 // Status of a CUDA runtime result.
