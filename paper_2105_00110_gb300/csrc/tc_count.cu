@@ -279,7 +279,7 @@ __device__ __forceinline__ uint32_t visit_octet(const LK& lk, const octet& o, in
         }
     }
     // the octet's 8 flag bits lie in one 32-bit word (pos is 8-aligned)
-    if (bits) atomicOr(&flag[pos >> 5], (uint32_t)bits << (pos & 31));
+    if (bits) flag_or(flag, pos >> 5, (uint32_t)bits << (pos & 31));
     return nh;
 }
 
@@ -311,7 +311,7 @@ __device__ __forceinline__ uint32_t visit_octet<lookup_bitmap, true>(const looku
     for (int k = 0; k < 8; ++k)
         if ((hm >> k) & 1u) atomicAdd(&cnt[l[k]], 1u);
     // the octet's 8 flag bits lie in one 32-bit word (pos is 8-aligned)
-    atomicOr(&flag[pos >> 5], hm << (pos & 31));
+    flag_or(flag, pos >> 5, hm << (pos & 31));
     return (uint32_t)__popc(hm);
 }
 

@@ -90,9 +90,15 @@ struct tc_graph {
 };
 
 // ---------------------------------------------------------------- helpers
-// Edge flags, one bit per CSR position.
+// Edge flags, one bit per CSR position.  Bits only ever turn on, so a read
+// that may be stale can only under-report set bits: an OR is issued only
+// when the word read lacks one of the bits, which skips the many repeated
+// settings of an edge that lies in several triangles.
+__device__ __forceinline__ void flag_or(uint32_t* __restrict__ fb, int64_t word, uint32_t mask) {
+    if ((fb[word] & mask) != mask) atomicOr(&fb[word], mask);
+}
 __device__ __forceinline__ void flag_set(uint32_t* __restrict__ fb, int64_t p) {
-    atomicOr(&fb[p >> 5], 1u << (p & 31));
+    flag_or(fb, p >> 5, 1u << (p & 31));
 }
 __device__ __forceinline__ bool flag_get(const uint32_t* __restrict__ fb, int64_t p) {
     return (fb[p >> 5] >> (p & 31)) & 1u;
