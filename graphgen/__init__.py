@@ -230,3 +230,24 @@ def single_triangle_with_pendants(pendants: int = 2):
         for _ in range(pendants):
             edges.append((v, nxt)); nxt += 1
     return _pairs(edges, nxt)
+
+
+def batch_config3(count: int = 8192, seed: int = 0x5EED0003, n_min: int = 32, n_max: int = 65536):
+    """The batched workload: `count` graphs, n log-uniform in [n_min, n_max];
+    half Barabasi-Albert with m uniform in 2..8, half planted hierarchies
+    (root joined to c in 4..32 cliques of size k in 3..12, leaves on clique
+    members, one noise edge per vertex with probability 0.01).  Graph i
+    draws from seed + i.  Returns a list of (src, dst, n)."""
+    graphs = []
+    for i in range(count):
+        s = seed + i
+        u = (gen_hash(s, 20, 0) >> 11) * (1.0 / 9007199254740992.0)
+        n = int(round(n_min * (n_max / n_min) ** u))
+        if gen_hash(s, 20, 1) & 1:
+            mm = 2 + int(gen_hash(s, 20, 2) % 7)
+            graphs.append(barabasi_albert(max(n, mm + 1), mm, s))
+        else:
+            c = 4 + int(gen_hash(s, 20, 3) % 29)
+            k = 3 + int(gen_hash(s, 20, 4) % 10)
+            graphs.append(planted_hierarchy(max(n, 1 + c * k), c, k, 0.01, s))
+    return graphs

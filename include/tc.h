@@ -198,6 +198,66 @@ tc_status tc_profile_read(tc_kernel_time* out, int cap, int* count);
 /* Number of kernels this library has launched since load (all threads). */
 int64_t tc_launch_count(void);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent graphs processed as one: the batch is the disjoint union
+ * of its graphs (graph k's vertices shifted by Σ_{j<k} n_j).  Triangles,
+ * counts, flags and numerators of a disjoint union are those of each graph,
+ * because Definition 1 only involves a vertex's neighbourhood; the only
+ * per-graph quantity is the denominator 3△(G_k) = Σ_{v ∈ G_k} △(v).  One
+ * build and one set of persistent count launches serve the whole batch.
+ */
+typedef struct tc_batch tc_batch;
+
+/*
+ * Builds a batch of num_graphs graphs.  Graph k has h_num_vertices[k]
+ * vertices and the pairs [h_pair_offsets[k], h_pair_offsets[k+1]) of
+ * src/dst, with ids local to the graph (in [0, n_k)).  h_pair_offsets
+ * (num_graphs + 1 entries, first 0) and h_num_vertices are host arrays;
+ * src/dst follow `flags` as in tc_build_csr.  Σ n_k must be < 2^31.
+ * Errors as tc_build_csr (a local id outside its graph gives
+ * TC_ERR_INVALID_ARG).  Synchronises `stream`.
+ */
+tc_status tc_batch_build(const void* src, const void* dst, const int64_t* h_pair_offsets,
+                         const int64_t* h_num_vertices, int64_t num_graphs, uint32_t flags,
+                         tc_stream stream, tc_batch** out);
+
+/*
+ * Counts and centrality of every graph of the batch.  Outputs are in union
+ * labels (graph k's vertex i at index voff[k] + i; its canonical edges at
+ * [eoff[k], eoff[k+1]) of the union edge list, see tc_batch_info); any may
+ * be NULL:
+ *   d_tri [Σn] uint64, d_edge_flag [Σm] uint8, d_numer [Σn] uint64,
+ *   d_tc [Σn] double (NaN on the vertices of a triangle-free graph),
+ *   d_tri_totals [num_graphs] uint64 = △(G_k).
+ * Makes no host synchronisation and no allocation, so it may be captured
+ * into a CUDA graph (after one plain run on the batch, which settles the
+ * kernels' launch attributes).
+ */
+tc_status tc_batch_run(tc_batch* b, uint64_t* d_tri, uint8_t* d_edge_flag, uint64_t* d_numer,
+                       double* d_tc, uint64_t* d_tri_totals, tc_stream stream);
+
+/* Shape of a batch; the offset arrays (num_graphs + 1 entries each, host
+ * memory, may be NULL) receive the vertex and canonical-edge offsets. */
+tc_status tc_batch_info(const tc_batch* b, int64_t* num_graphs, int64_t* num_vertices,
+                        int64_t* num_edges, int64_t* h_vertex_offsets, int64_t* h_edge_offsets);
+
+/* The union's canonical edge list (union labels), as tc_copy_edges. */
+tc_status tc_batch_copy_edges(const tc_batch* b, int32_t* d_u, int32_t* d_v, tc_stream stream);
+
+tc_status tc_batch_get_stats(const tc_batch* b, tc_graph_stats* out);
+
+/*
+ * Autotuner: times the count step of this batch under several planner
+ * settings (when a vertex is heavy enough for a CTA item; the work carried
+ * by one CTA item and one warp item), `reps` runs each, keeps the fastest.
+ * Synchronises `stream`.  tc_batch_get_params reports the chosen setting as
+ * {cta_min_work, cta_chunk, warp_chunk}.
+ */
+tc_status tc_batch_autotune(tc_batch* b, int reps, tc_stream stream);
+tc_status tc_batch_get_params(const tc_batch* b, int64_t* out3);
+
+void tc_batch_free(tc_batch* b);
+
 /* Releases g.  Its device memory is freed in stream order on the stream of
  * the last call made on g, which must still exist. */
 void tc_graph_free(tc_graph* g);

@@ -41,7 +41,9 @@ STRATEGIES = {"auto": 0, "bsearch": 1, "merge": 2, "bitmap": 3, "global": 4}
 EXPORTED = ["tc_build_csr", "tc_count", "tc_centrality", "tc_divide", "tc_graph_info",
             "tc_copy_edges", "tc_get_stats", "tc_set_strategy", "tc_profile_enable",
             "tc_profile_reset", "tc_profile_read", "tc_launch_count", "tc_graph_free",
-            "tc_status_str"]
+            "tc_status_str", "tc_batch_build", "tc_batch_run", "tc_batch_info",
+            "tc_batch_copy_edges", "tc_batch_get_stats", "tc_batch_autotune", "tc_batch_get_params",
+            "tc_batch_free"]
 
 
 class TCError(RuntimeError):
@@ -119,6 +121,22 @@ def lib():
         L.tc_graph_free.argtypes = [vp]
         L.tc_status_str.restype = ctypes.c_char_p
         L.tc_status_str.argtypes = [i32]
+        L.tc_batch_build.restype = i32
+        L.tc_batch_build.argtypes = [vp, vp, vp, vp, i64, u32, vp, ctypes.POINTER(vp)]
+        L.tc_batch_run.restype = i32
+        L.tc_batch_run.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.tc_batch_info.restype = i32
+        L.tc_batch_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64), vp, vp]
+        L.tc_batch_copy_edges.restype = i32
+        L.tc_batch_copy_edges.argtypes = [vp, vp, vp, vp]
+        L.tc_batch_get_stats.restype = i32
+        L.tc_batch_get_stats.argtypes = [vp, ctypes.POINTER(GraphStats)]
+        L.tc_batch_autotune.restype = i32
+        L.tc_batch_autotune.argtypes = [vp, i32, vp]
+        L.tc_batch_get_params.restype = i32
+        L.tc_batch_get_params.argtypes = [vp, vp]
+        L.tc_batch_free.restype = None
+        L.tc_batch_free.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -302,3 +320,105 @@ def triangle_centrality(src, dst, n: int, strategy=None, stream=None) -> dict:
                     status=st, edge_u=eu, edge_v=ev, stats=g.stats())
     finally:
         g.close()
+
+
+# ------------------------------------------------------------------ batches
+def pack_graphs(graphs):
+    """[(src, dst, n), ...] with local ids -> (src, dst, pair_offsets, num_vertices)."""
+    srcs = [np.ascontiguousarray(g[0], dtype=np.int32) for g in graphs]
+    dsts = [np.ascontiguousarray(g[1], dtype=np.int32) for g in graphs]
+    nv = np.array([int(g[2]) for g in graphs], dtype=np.int64)
+    off = np.zeros(len(graphs) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(x) for x in srcs])
+    src = np.concatenate(srcs) if srcs else np.zeros(0, np.int32)
+    dst = np.concatenate(dsts) if dsts else np.zeros(0, np.int32)
+    return src, dst, off, nv
+
+
+def tc_batch_build(src, dst, pair_offsets, num_vertices, stream=None):
+    if isinstance(src, np.ndarray):
+        src = torch.from_numpy(np.ascontiguousarray(src))
+    if isinstance(dst, np.ndarray):
+        dst = torch.from_numpy(np.ascontiguousarray(dst))
+    if src.dtype != dst.dtype or src.shape != dst.shape or src.dtype not in (torch.int32, torch.int64):
+        raise ValueError("src/dst must be 1-D int32 or int64 of equal length")
+    src, dst = src.contiguous(), dst.contiguous()
+    off = np.ascontiguousarray(pair_offsets, dtype=np.int64)
+    nv = np.ascontiguousarray(num_vertices, dtype=np.int64)
+    if len(off) != len(nv) + 1:
+        raise ValueError("pair_offsets needs num_graphs + 1 entries")
+    flags = (TC_IDS_INT32 if src.dtype == torch.int32 else 0) | (TC_IN_DEVICE if src.is_cuda else 0)
+    h = ctypes.c_void_p()
+    st = lib().tc_batch_build(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                              ctypes.c_void_p(off.ctypes.data), ctypes.c_void_p(nv.ctypes.data),
+                              len(nv), flags, _stream(stream), ctypes.byref(h))
+    _check(st, "tc_batch_build", ok=(TC_OK,))
+    return h
+
+
+def tc_batch_run(b, tri=None, edge_flag=None, numer=None, tc=None, totals=None, stream=None):
+    st = lib().tc_batch_run(b, _dptr(tri), _dptr(edge_flag), _dptr(numer), _dptr(tc), _dptr(totals),
+                            _stream(stream))
+    _check(st, "tc_batch_run", ok=(TC_OK,))
+
+
+def tc_batch_info(b):
+    G, n, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().tc_batch_info(b, ctypes.byref(G), ctypes.byref(n), ctypes.byref(m), None, None),
+           "tc_batch_info", ok=(TC_OK,))
+    voff = np.zeros(G.value + 1, dtype=np.int64)
+    eoff = np.zeros(G.value + 1, dtype=np.int64)
+    lib().tc_batch_info(b, None, None, None, ctypes.c_void_p(voff.ctypes.data), ctypes.c_void_p(eoff.ctypes.data))
+    return G.value, n.value, m.value, voff, eoff
+
+
+class Batch:
+    """Owns a tc_batch; results are CUDA tensors in union labels."""
+
+    def __init__(self, src, dst, pair_offsets, num_vertices, stream=None):
+        self.h = tc_batch_build(src, dst, pair_offsets, num_vertices, stream)
+        self.G, self.n, self.m, self.voff, self.eoff = tc_batch_info(self.h)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.out = dict(
+            tri=torch.empty(max(self.n, 1), dtype=torch.uint64, device=self.device),
+            flag=torch.empty(max(self.m, 1), dtype=torch.uint8, device=self.device),
+            numer=torch.empty(max(self.n, 1), dtype=torch.uint64, device=self.device),
+            tc=torch.empty(max(self.n, 1), dtype=torch.float64, device=self.device),
+            totals=torch.empty(max(self.G, 1), dtype=torch.uint64, device=self.device))
+
+    def close(self):
+        if self.h:
+            lib().tc_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, stream=None):
+        o = self.out
+        tc_batch_run(self.h, o["tri"], o["flag"], o["numer"], o["tc"], o["totals"], stream)
+        return o
+
+    def edges(self):
+        u = torch.empty(max(self.m, 1), dtype=torch.int32, device=self.device)
+        v = torch.empty(max(self.m, 1), dtype=torch.int32, device=self.device)
+        _check(lib().tc_batch_copy_edges(self.h, _dptr(u), _dptr(v), _stream(None)), "tc_batch_copy_edges",
+               ok=(TC_OK,))
+        return u[: self.m], v[: self.m]
+
+    def autotune(self, reps: int = 2, stream=None):
+        _check(lib().tc_batch_autotune(self.h, int(reps), _stream(stream)), "tc_batch_autotune", ok=(TC_OK,))
+        return self.params()
+
+    def params(self):
+        out = np.zeros(3, dtype=np.int64)
+        lib().tc_batch_get_params(self.h, ctypes.c_void_p(out.ctypes.data))
+        return dict(cta_min_work=int(out[0]), cta_chunk=int(out[1]), warp_chunk=int(out[2]))
+
+    def stats(self) -> dict:
+        st = GraphStats()
+        _check(lib().tc_batch_get_stats(self.h, ctypes.byref(st)), "tc_batch_get_stats", ok=(TC_OK,))
+        return st.as_dict()

@@ -30,6 +30,7 @@
 #include <cub/cub.cuh>
 
 #include <algorithm>
+#include <mutex>
 
 #include "tc_internal.cuh"
 
@@ -49,9 +50,6 @@ constexpr int kCtaWarps = TC_CTA_THREADS / 32;
 constexpr int64_t kBitmapSmallSmem = 32 * 1024;   // dynamic smem of the small-bitmap CTA kernel (5 CTAs per SM)
 constexpr int64_t kBitmapLargeSmem = 100 * 1024;  // ... of the large-bitmap CTA kernel
 constexpr int64_t kCtaListSmem = 100 * 1024;      // ... of the CTA sorted-list kernel
-constexpr int64_t kCtaChunk = 65536;              // target wedges per CTA item
-constexpr int64_t kWarpChunk = 16384;             // target wedges per warp item
-constexpr int64_t kCtaMinWork = 4096;             // below this a vertex is a warp item
 
 enum { L_BITMAP = 0, L_SORTED = 1, L_GLOBAL = 2 };
 
@@ -649,7 +647,7 @@ struct class_acc {
 // rank order so that the heaviest vertices come first in every class.
 __global__ void k_classify(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
                            const int32_t* __restrict__ col, const int64_t* __restrict__ work,
-                           int64_t n, int strategy, int64_t* __restrict__ cnt,
+                           int64_t n, int strategy, tc_plan_params pp, int64_t* __restrict__ cnt,
                            int8_t* __restrict__ cls, class_acc* __restrict__ acc) {
     ull loc[4][TC_NUM_CLS] = {};   // per-thread sums, reduced per warp at the end
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -676,7 +674,7 @@ __global__ void k_classify(const int64_t* __restrict__ row_ptr, const int64_t* _
             } else {
                 // AUTO: heavy vertices on a CTA bitmap when zeroing it is cheap
                 // next to the work; the rest on a warp (bitmap or list)
-                const bool heavy = W >= kCtaMinWork && W >= 2 * words;
+                const bool heavy = W >= pp.cta_min_work && W >= 2 * words;
                 if (heavy && !warp_bm && cta_s) c = TC_CLS_BITMAP_S;
                 else if (heavy && !warp_bm && cta_l) c = TC_CLS_BITMAP_L;
                 else if (warp_bm || warp_list) c = TC_CLS_WARP;
@@ -684,7 +682,7 @@ __global__ void k_classify(const int64_t* __restrict__ row_ptr, const int64_t* _
                 else if (cta_l) c = TC_CLS_BITMAP_L;
                 else c = TC_CLS_CTA_LIST;
             }
-            const int64_t chunk = c == TC_CLS_WARP ? kWarpChunk : kCtaChunk;
+            const int64_t chunk = c == TC_CLS_WARP ? pp.warp_chunk : pp.cta_chunk;
             chunks = (W + chunk - 1) / chunk;
             if (chunks > lv) chunks = lv;
             if (chunks < 1) chunks = 1;
@@ -742,15 +740,38 @@ inline int blocks_for(int64_t items) {
     return (int)std::max<int64_t>(1, std::min(b, cap));
 }
 
+// Per-kernel launch shape, computed once (so that later launches, e.g.
+// inside a stream capture, make no attribute or occupancy calls).
+struct launch_shape {
+    const void* fn;
+    size_t smem;
+    int per_sm;
+};
+std::mutex g_shape_mu;
+launch_shape g_shapes[32];
+int g_nshapes = 0;
+
+tc_status shape_for(const void* fn, size_t smem, int& per_sm) {
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    for (int i = 0; i < g_nshapes; ++i)
+        if (g_shapes[i].fn == fn && g_shapes[i].smem == smem) {
+            per_sm = g_shapes[i].per_sm;
+            return TC_OK;
+        }
+    // static + dynamic shared memory may exceed the 48 KB default
+    if (smem > 0) TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TC_CTA_THREADS, smem));
+    per_sm = std::max(per_sm, 1);
+    if (g_nshapes < 32) g_shapes[g_nshapes++] = launch_shape{fn, smem, per_sm};
+    return TC_OK;
+}
+
 template <class K>
 tc_status launch_persistent(K kernel, const char* name, size_t smem, int64_t items, cudaStream_t s,
                             const tc_graph* g, const tc_plan& p, int c, ull* cursor) {
     if (items == 0) return TC_OK;
-    // static + dynamic shared memory may exceed the 48 KB default
-    if (smem > 0) TC_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, TC_CTA_THREADS, smem));
-    per_sm = std::max(per_sm, 1);
+    int per_sm = 1;
+    TC_TRY(shape_for((const void*)kernel, smem, per_sm));
     int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, items);
     launch_scope ls(name, s);
     kernel<<<(int)blocks, TC_CTA_THREADS, smem, s>>>(g->row_ptr, g->col, g->hstart, g->head,
@@ -810,7 +831,7 @@ tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s) {
     if (n > 0) {
         launch_scope ls("plan_classify", s);
         k_classify<<<blocks_for(n), 256, 0, s>>>(g->row_ptr, g->hstart, g->col, g->work, n, strategy,
-                                                  cnt, cls, acc);
+                                                  g->params, cnt, cls, acc);
         PLAN_CUDA(cudaGetLastError());
     }
     PLAN_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, cnt, off, n + 1, s));
@@ -842,6 +863,7 @@ tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s) {
     p.smem[TC_CLS_WARP] = 0;
     p.smem[TC_CLS_CTA_LIST] = kCtaListSmem;
     p.strategy = strategy;
+    g->plan_params_version = g->params_version;
     // algorithmic bytes of each class's kernel: stage N_H(v) once (4 hv),
     // read each head entry's label, twin and stream length (16), stream each
     // wedge id (4)
@@ -861,7 +883,8 @@ tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s) {
 
 tc_status run_count(tc_graph* g, cudaStream_t s) {
     const int64_t n = g->n, e2 = 2 * g->m;
-    if (g->plan.strategy != g->strategy) TC_TRY(make_plan(g, g->strategy, s));
+    if (g->plan.strategy != g->strategy || g->plan_params_version != g->params_version)
+        TC_TRY(make_plan(g, g->strategy, s));
     TC_CUDA(cudaMemsetAsync(g->tri, 0, (n + 1) * 8, s));
     TC_CUDA(cudaMemsetAsync(g->flag, 0, flag_words(e2) * 4, s));
     TC_CUDA(cudaMemsetAsync(g->counters, 0, 8 * 8, s));

@@ -71,14 +71,8 @@ __device__ __forceinline__ ull warp_sum(ull x) {
 // the twin position where its flag sits.
 // Rows are in rank (= degree) order, so three contiguous rank bands get
 // one thread, one warp and one CTA per row.
-__device__ __forceinline__ void finish_row(int64_t r, ull acc, const int32_t* __restrict__ perm, ull den,
-                                           ull* __restrict__ numer_rank, ull* __restrict__ numer_out,
-                                           double* __restrict__ tc_out) {
-    numer_rank[r] = acc;
-    const int32_t v = perm[r];
-    if (numer_out) numer_out[v] = acc;
-    if (tc_out) tc_out[v] = div_rn(acc, den);
-}
+struct gather_args;
+__device__ __forceinline__ void finish_row(int64_t r, ull acc, const gather_args& a);
 
 struct gather_args {
     const int64_t* row_ptr;
@@ -89,10 +83,19 @@ struct gather_args {
     const ull* tri;
     const int32_t* perm;
     ull den;
+    const int32_t* rank_graph;   // batches: graph of each rank, or null
+    const ull* den_graph;        // batches: 3△ of each graph
     ull* numer_rank;
     ull* numer_out;
     double* tc_out;
 };
+
+__device__ __forceinline__ void finish_row(int64_t r, ull acc, const gather_args& a) {
+    a.numer_rank[r] = acc;
+    const int32_t v = a.perm[r];
+    if (a.numer_out) a.numer_out[v] = acc;
+    if (a.tc_out) a.tc_out[v] = div_rn(acc, a.rank_graph ? a.den_graph[a.rank_graph[r]] : a.den);
+}
 
 // one thread per row, rows [r0, r1)
 __global__ void __launch_bounds__(256) k_gather_thread(gather_args a, int64_t r0, int64_t r1) {
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(256) k_gather_thread(gather_args a, int64_t r0
             acc += (flag_get(a.flag, rec.twin) ? 1ull : 3ull) * a.tri[rec.u];
         }
         for (int64_t p = h; p < e; ++p) acc += (flag_get(a.flag, p) ? 1ull : 3ull) * a.tri[a.col[p]];
-        finish_row(r, acc, a.perm, a.den, a.numer_rank, a.numer_out, a.tc_out);
+        finish_row(r, acc, a);
     }
 }
 
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(256) k_gather_warp(gather_args a, int64_t r0, 
         }
         for (int64_t p = h + lane; p < e; p += 32) acc += (flag_get(a.flag, p) ? 1ull : 3ull) * a.tri[a.col[p]];
         acc = warp_sum(acc);
-        if (lane == 0) finish_row(r, acc + a.tri[r], a.perm, a.den, a.numer_rank, a.numer_out, a.tc_out);
+        if (lane == 0) finish_row(r, acc + a.tri[r], a);
     }
 }
 
@@ -144,9 +147,24 @@ __global__ void __launch_bounds__(1024) k_gather_cta(gather_args a, int64_t r0, 
         if (warp == 0) {
             ull x = lane < (int)(blockDim.x >> 5) ? part[lane] : 0ull;
             x = warp_sum(x);
-            if (lane == 0) finish_row(r, x + a.tri[r], a.perm, a.den, a.numer_rank, a.numer_out, a.tc_out);
+            if (lane == 0) finish_row(r, x + a.tri[r], a);
         }
         __syncthreads();
+    }
+}
+
+// Σ_{v ∈ graph k} △(v) (= 3△(G_k)) for every graph of a batch; lanes of a
+// warp that hit the same graph add once.
+__global__ void k_graph_sums(const ull* __restrict__ tri, const int32_t* __restrict__ rank_graph, int64_t n,
+                             ull* __restrict__ sums) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = rank_graph[r];
+        const ull t = tri[r];
+        const unsigned same = __match_any_sync(__activemask(), k);
+        ull sum = 0;
+        for (unsigned mm = same; mm; mm &= mm - 1) sum += __shfl_sync(same, t, __ffs(mm) - 1);
+        if ((threadIdx.x & 31) == __ffs(same) - 1 && sum) atomicAdd(&sums[k], sum);
     }
 }
 
@@ -183,7 +201,7 @@ tc_status run_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, cudaStrea
     const int64_t n = g->n;
     if (n == 0) return TC_OK;
     gather_args a{g->row_ptr, g->hstart, g->col, g->head, g->flag, g->tri, g->perm,
-                  3ull * (ull)g->total, g->numer, (ull*)d_numer, d_tc};
+                  3ull * (ull)g->total, g->rank_graph, g->den_graph, g->numer, (ull*)d_numer, d_tc};
     const int64_t r1 = g->band[0], r2 = g->band[1];   // degree <= 32 | <= 4096 | larger
     if (r1 > 0) {
         launch_scope ls("gather_thread", s);
@@ -201,6 +219,14 @@ tc_status run_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, cudaStrea
         k_gather_cta<<<(int)std::min<int64_t>(rows, (int64_t)sm_count() * 2), 1024, 0, s>>>(a, r2, n);
         TC_LAUNCH_CHECK();
     }
+    return TC_OK;
+}
+
+tc_status run_graph_sums(tc_graph* g, const int32_t* rank_graph, ull* sums, cudaStream_t s) {
+    if (g->n == 0) return TC_OK;
+    launch_scope ls("batch_graph_sums", s);
+    k_graph_sums<<<blocks_for(g->n, 256), 256, 0, s>>>(g->tri, rank_graph, g->n, sums);
+    TC_LAUNCH_CHECK();
     return TC_OK;
 }
 

@@ -51,6 +51,13 @@ struct __align__(16) tc_head {
     int64_t twin;
 };
 
+// Planner parameters (tuned per batch by tc_batch_autotune).
+struct tc_plan_params {
+    int64_t cta_min_work = 4096;   // W(v) at or above which v may become CTA items
+    int64_t cta_chunk = 65536;     // target wedges per CTA item
+    int64_t warp_chunk = 16384;    // target wedges per warp item
+};
+
 struct tc_plan {
     int strategy = -1;                 // strategy the plan was made for
     int64_t count[TC_NUM_CLS] = {};
@@ -86,7 +93,12 @@ struct tc_graph {
     int counted = 0;
     uint64_t total = 0;
     int strategy = TC_STRATEGY_AUTO;
+    tc_plan_params params;
+    int plan_params_version = 0, params_version = 0;
     tc_graph_stats stats{};
+    // optional per-graph denominators (batches): rank -> graph, Σ△(v) per graph
+    const int32_t* rank_graph = nullptr;
+    const unsigned long long* den_graph = nullptr;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -135,6 +147,7 @@ void free_plan(tc_plan& p, cudaStream_t s);
 tc_status run_count(tc_graph* g, cudaStream_t s);
 // gather + divide (tc_gather.cu)
 tc_status run_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, cudaStream_t s);
+tc_status run_graph_sums(tc_graph* g, const int32_t* rank_graph, unsigned long long* sums, cudaStream_t s);
 tc_status run_divide(const uint64_t* d_numer, int64_t n, uint64_t den, double* d_tc, cudaStream_t s);
 tc_status export_tri(tc_graph* g, uint64_t* d_tri, cudaStream_t s);
 tc_status export_flags(tc_graph* g, uint8_t* d_flag, cudaStream_t s);
