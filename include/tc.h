@@ -258,6 +258,48 @@ tc_status tc_batch_get_params(const tc_batch* b, int64_t* out3);
 
 void tc_batch_free(tc_batch* b);
 
+/*
+ * Triangle counts, numerators and TC of a small graph given as a device
+ * CSR, computed without allocating memory of any kind.  The paper has no
+ * counterpart: this is a service for callers that cannot let a library
+ * allocate — a runtime that owns all device memory through its own
+ * allocator, a latency-critical loop that must not wait on pool growth, a
+ * program whose memory footprint is fixed up front.  The results are those
+ * of tc_count followed by tc_centrality on the same graph (Definition 1;
+ * numerator and single division of Algorithm 2), bit for bit.
+ *
+ *   d_row_ptr  [n+1] int64, device: row v is d_col[d_row_ptr[v] ..
+ *              d_row_ptr[v+1]); d_row_ptr[0] = 0, d_row_ptr[n] = nnz.
+ *   d_col      [nnz] int32, device: neighbour ids in [0, n), each row
+ *              strictly increasing (sorted, no duplicates), no self loops,
+ *              symmetric (u in row v exactly when v in row u).
+ *   n, nnz     0 <= n <= TC_NOALLOC_MAX_VERTICES, 0 <= nnz <=
+ *              TC_NOALLOC_MAX_ENTRIES, nnz even (= 2m).
+ *   d_tri      [n] uint64, device: △(v).  May be NULL.
+ *   d_numer    [n] uint64, device: numer(v) = 3△(G)·TC(v).  May be NULL.
+ *   d_tc       [n] double, device: TC(v); NaN everywhere if △(G) = 0.
+ *              May be NULL.
+ * Working memory is one fixed 768 KB array per device inside the library
+ * (counts, edge flags, 3△(G), an error word); each call clears what it
+ * uses first.  The first call on a device looks up that array's address
+ * (with lazy module loading, it may also load the library's device code):
+ * make that first call outside any stream capture.  Because the array is
+ * shared, calls on the same device must not overlap: two calls in flight
+ * at once, on different streams or threads, corrupt each other's results.
+ * Order them on one stream, or with events.
+ * Returns TC_ERR_INVALID_ARG, without touching the device, for sizes beyond
+ * the limits, odd nnz or NULL inputs; TC_ERR_CUDA if the address lookup or
+ * a launch fails; otherwise TC_OK once the work is enqueued on `stream`
+ * (not synchronised; △(G) = 0 is not reported here).  An input that breaks
+ * the CSR rules above is detected on the device: every d_tri and d_numer
+ * entry is then UINT64_MAX and every d_tc entry NaN.
+ */
+#define TC_NOALLOC_MAX_VERTICES 65536
+#define TC_NOALLOC_MAX_ENTRIES 2097152
+tc_status tc_csr_centrality_noalloc(const int64_t* d_row_ptr, const int32_t* d_col, int64_t n,
+                                    int64_t nnz, uint64_t* d_tri, uint64_t* d_numer, double* d_tc,
+                                    tc_stream stream);
+
 /* Releases g.  Its device memory is freed in stream order on the stream of
  * the last call made on g, which must still exist. */
 void tc_graph_free(tc_graph* g);

@@ -43,7 +43,7 @@ EXPORTED = ["tc_build_csr", "tc_count", "tc_centrality", "tc_divide", "tc_graph_
             "tc_profile_reset", "tc_profile_read", "tc_launch_count", "tc_graph_free",
             "tc_status_str", "tc_batch_build", "tc_batch_run", "tc_batch_info",
             "tc_batch_copy_edges", "tc_batch_get_stats", "tc_batch_autotune", "tc_batch_get_params",
-            "tc_batch_free"]
+            "tc_batch_free", "tc_csr_centrality_noalloc"]
 
 
 class TCError(RuntimeError):
@@ -137,6 +137,8 @@ def lib():
         L.tc_batch_get_params.argtypes = [vp, vp]
         L.tc_batch_free.restype = None
         L.tc_batch_free.argtypes = [vp]
+        L.tc_csr_centrality_noalloc.restype = i32
+        L.tc_csr_centrality_noalloc.argtypes = [vp, vp, i64, i64, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -211,6 +213,25 @@ def tc_centrality(g, numer=None, tc=None, stream=None):
 def tc_divide(numer, den: int, out, stream=None):
     st = lib().tc_divide(_dptr(numer), numer.numel(), int(den), _dptr(out), _stream(stream))
     _check(st, "tc_divide", ok=(TC_OK,))
+
+
+TC_NOALLOC_MAX_VERTICES = 65536
+TC_NOALLOC_MAX_ENTRIES = 2097152
+
+
+def tc_csr_centrality_noalloc(row_ptr, col, n: int, tri=None, numer=None, tc=None, stream=None):
+    """Counts, numerators and TC of a small graph given as a device CSR
+    (row_ptr [n+1] int64, col [nnz] int32; sorted, symmetric, no loops),
+    using only the library's fixed working array: nothing is allocated.
+    Outputs are caller tensors (tri/numer uint64 [n], tc float64 [n]).
+    Calls on one device must not overlap in time."""
+    for t, dt in ((row_ptr, torch.int64), (col, torch.int32)):
+        if t.dtype != dt:
+            raise ValueError("row_ptr must be int64 and col int32")
+    st = lib().tc_csr_centrality_noalloc(_dptr(row_ptr), _dptr(col) if col.numel() else None, int(n),
+                                         col.numel(), _dptr(tri), _dptr(numer), _dptr(tc),
+                                         _stream(stream))
+    _check(st, "tc_csr_centrality_noalloc", ok=(TC_OK,))
 
 
 def tc_graph_info(g):

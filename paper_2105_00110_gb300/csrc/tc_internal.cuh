@@ -127,6 +127,7 @@ tc_status dalloc(void** p, size_t bytes, cudaStream_t s);
 void dfree(void* p, cudaStream_t s);
 
 // Launch accounting and optional per-kernel event timing.
+void add_launches(int64_t k);   // counts launches made without note_launch
 void note_launch(const char* name, cudaStream_t s, int phase);  // phase 0 before, 1 after
 struct launch_scope {
     const char* name; cudaStream_t s;
