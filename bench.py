@@ -40,6 +40,10 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "rmat-s24-ef16"
 BATCH_WORKLOADS = {"batched-8192": dict(kind="batch", count=8192, seed=0x5EED0003)}
+SERVED_WORKLOADS = {"served-poisson": dict(kind="served", rate=2000.0, duration=60.0, pool=256,
+                                           e_min=1e3, e_max=1e8, budget=150 * 10**9,
+                                           max_batch_pairs=1 << 25, workers=2,
+                                           sustain_duration=30.0, sustain_load=0.75, seed=0x5EED0004)}
 
 
 def generate(spec: dict, rank: int = 0):
@@ -441,6 +445,174 @@ def run_batched(args, spec, wl_name):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------- served path
+def _pct(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
+
+
+def _mem_available():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def run_served(args, spec, wl_name):
+    """Served workload: a Poisson request stream over a pre-generated pool of
+    graphs in pinned host memory, through the request loop (tc_server_*).
+    Every request crosses host -> device -> host.  Two phases: the stated
+    arrival rate for the stated duration (offered load far beyond capacity:
+    throughput is what completes inside the window, latency is that of the
+    requests completed in it, the rest are dropped at the end and counted),
+    then a rate of sustain_load x the measured request capacity, drained to
+    the last request, whose latencies are the steady-state figures."""
+    import numpy as np
+    import torch
+
+    import graphgen as gg
+    import paper_2105_00110_gb300 as tcg
+
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    tcg.build()
+    pool_seed = spec["seed"] + 0x100000 * rank
+    specs = gg.served_pool_specs(spec["pool"], pool_seed, spec["e_min"], spec["e_max"])
+    need = sum(8 * sp["pairs"] + 16 * (2 ** sp["scale"] if sp["kind"] == "rmat" else sp["side"] ** 2)
+               for sp in specs)
+    avail = _mem_available()
+    if avail is not None and need > 0.4 * avail:
+        raise SystemExit("served pool needs %.1f GB of pinned host memory, %.1f GB available"
+                         % (need / 1e9, avail / 1e9))
+    tg0 = time.perf_counter()
+    pool = []
+    for sp in specs:
+        s_, d_, n_ = gg.served_graph(sp)
+        hs = torch.from_numpy(s_).pin_memory()
+        hd = torch.from_numpy(d_).pin_memory()
+        # results of every request of this pool entry land here; requests of
+        # the same entry write identical values
+        tri = torch.empty(max(n_, 1), dtype=torch.int64).pin_memory().view(torch.uint64)
+        tcv = torch.empty(max(n_, 1), dtype=torch.float64).pin_memory()
+        pool.append((hs, hd, n_, tri, tcv))
+        del s_, d_
+    gen_s = time.perf_counter() - tg0
+
+    def new_server():
+        return tcg.Server(spec["budget"], spec["max_batch_pairs"], spec["workers"])
+
+    # warm-up pass: every pool graph once (also gives m and triangles per entry)
+    srv = new_server()
+    ids = {srv.submit(hs, hd, n_, tri, tcv): i for i, (hs, hd, n_, tri, tcv) in enumerate(pool)}
+    m_of, tri_of = {}, {}
+    for r in srv.wait_all(900):
+        m_of[ids[r["id"]]] = r["edges"]
+        tri_of[ids[r["id"]]] = r["triangles"]
+    srv.close()
+    assert len(m_of) == len(pool), "warm-up pass incomplete"
+
+    def run_phase(rate, duration, seed, drain):
+        rng = np.random.default_rng(seed)
+        k = int(rate * duration * 1.2) + 16
+        arr = np.cumsum(rng.exponential(1.0 / rate, k))
+        arr = arr[arr < duration]
+        pick = rng.integers(0, len(pool), len(arr))
+        srv = new_server()
+        req_of = {}
+        done = []
+        lag = 0.0
+        launches0 = tcg.tc_launch_count()
+        t0 = time.perf_counter()
+        srv_t0 = None
+        j = 0
+        while j < len(arr):
+            now = time.perf_counter() - t0
+            while j < len(arr) and arr[j] <= now:
+                hs, hd, n_, tri, tcv = pool[pick[j]]
+                rid = srv.submit(hs, hd, n_, tri, tcv)
+                req_of[rid] = (int(pick[j]), float(arr[j]))
+                lag = max(lag, now - arr[j])
+                j += 1
+            done += srv.poll(4096)
+            if j < len(arr):
+                wait = arr[j] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.002))
+        t_end = time.perf_counter() - t0
+        if drain:
+            done += srv.wait_all(1800)
+            t_end = time.perf_counter() - t0
+        else:
+            while True:
+                got = srv.poll(4096)
+                done += got
+                if len(got) < 4096:
+                    break
+        st = srv.stats()
+        launches = tcg.tc_launch_count() - launches0
+        srv.close()
+        # server clock: t_submit of the first request is about t = 0 here
+        first = min((r["t_submit"] for r in done), default=0.0)
+        window = duration if not drain else max(r["t_done"] for r in done) - first
+        inside = [r for r in done if drain or r["t_done"] - first <= duration]
+        lat = [1e3 * (r["t_done"] - r["t_submit"]) for r in inside]
+        bad = [r for r in inside if r["status"] < 0 or r["triangles"] != tri_of[req_of[r["id"]][0]]]
+        edges = sum(r["edges"] for r in inside)
+        pairs = sum(len(pool[req_of[r["id"]][0]][0]) for r in inside)
+        half = [1e3 * (r["t_done"] - r["t_submit"]) for r in inside if req_of[r["id"]][1] < duration / 2]
+        half2 = [1e3 * (r["t_done"] - r["t_submit"]) for r in inside if req_of[r["id"]][1] >= duration / 2]
+        mean_pairs = float(np.mean([len(pool[p][0]) for p in pick])) if len(pick) else 0.0
+        return {
+            "rate_req_s": rate, "arrivals_s": duration, "submitted": int(len(arr)),
+            "completed": len(inside), "dropped_or_late": int(len(arr)) - len(inside),
+            "window_s": window, "achieved_req_s": len(inside) / window,
+            "achieved_edges_per_s": edges / window, "achieved_pairs_per_s": pairs / window,
+            "offered_pairs_per_s": rate * mean_pairs,
+            "latency_ms": {"p50": _pct(lat, 50), "p99": _pct(lat, 99), "max": max(lat) if lat else None},
+            "p99_first_half_ms": _pct(half, 99), "p99_second_half_ms": _pct(half2, 99),
+            "batch_size_mean": float(np.mean([r["batch_size"] for r in inside])) if inside else None,
+            "batches": st["batches"], "submit_lag_ms_max": 1e3 * lag, "wrong_results": len(bad),
+            "gpu_launches": int(launches), "edges": edges,
+            "h2d_bytes": 8 * pairs, "d2h_bytes": 16 * sum(pool[req_of[r["id"]][0]][2] for r in inside),
+        }
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(1.0)
+    h0 = time.time()
+    over = run_phase(spec["rate"], spec["duration"], pool_seed + 1, drain=False)
+    h1 = time.time()
+    clocks = sampler.stop(h0, h1)
+    sus_rate = max(1.0, spec["sustain_load"] * over["achieved_req_s"])
+    sus = run_phase(sus_rate, spec["sustain_duration"], pool_seed + 2, drain=True)
+    if rank == 0:
+        n_done = max(over["completed"], 1)
+        print(json.dumps({
+            "metric": METRIC + "; p50/p99 request latency", "value": over["achieved_edges_per_s"],
+            "unit": "edges/s", "n_gpus": 1, "steps": over["completed"], "warmup": len(pool),
+            "ms_per_step": 1e3 * over["window_s"] / n_done, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": wl_name, "pool_graphs": len(pool),
+                       "pool_pairs": int(sum(len(p[0]) for p in pool)), "generator": spec,
+                       "step": "one request (host pairs in, host results out)",
+                       "l2": "inputs larger than L2 (pool %.1f GB of pinned pairs, requests drawn at random)"
+                             % (sum(len(p[0]) for p in pool) * 8 / 1e9),
+                       "pool_generation_s": round(gen_s, 1), "parallelism": "single"},
+            "clocks": clocks,
+            "e2e": {"value": over["achieved_edges_per_s"], "unit": "edges/s",
+                    "h2d_bytes_per_step": over["h2d_bytes"] // n_done,
+                    "d2h_bytes_per_step": over["d2h_bytes"] // n_done},
+            "gpu_launches": over["gpu_launches"], "roofline": None, "cpu_baseline": None,
+            "latency_ms": over["latency_ms"],
+            "overload": over, "sustainable": sus,
+        }))
+
+
 # ------------------------------------------------------------- oracle side
 CPU_SAMPLE = dict(kind="rmat", scale=18, edge_factor=16, seed=0x5EED0012)
 
@@ -495,7 +667,7 @@ def main(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(SERVED_WORKLOADS))
     ap.add_argument("--baseline-graphs", type=int, default=8192,
                     help="graphs timed one launch per graph (batched workloads)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -505,6 +677,8 @@ def main(argv=None):
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         run_reference(args, args.workload)
+    elif args.workload in SERVED_WORKLOADS:
+        run_served(args, SERVED_WORKLOADS[args.workload], args.workload)
     elif args.workload in BATCH_WORKLOADS:
         run_batched(args, BATCH_WORKLOADS[args.workload], args.workload)
     else:

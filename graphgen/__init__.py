@@ -251,3 +251,51 @@ def batch_config3(count: int = 8192, seed: int = 0x5EED0003, n_min: int = 32, n_
             k = 3 + int(gen_hash(s, 20, 4) % 10)
             graphs.append(planted_hierarchy(max(n, 1 + c * k), c, k, 0.01, s))
     return graphs
+
+
+def _unit(seed: int, stream: int, ctr: int) -> float:
+    return (gen_hash(seed, stream, ctr) >> 11) * (1.0 / 9007199254740992.0)
+
+
+def served_pool_specs(count: int = 256, seed: int = 0x5EED0004, e_min: float = 1e3, e_max: float = 1e8,
+                      cl_share: float = 0.25):
+    """The served workload's request pool: `count` graph specs whose pair
+    counts E are stratified over the log-uniform law on [e_min, e_max]
+    (pool entry i draws its quantile from stratum i, then the entries are
+    shuffled).  Each is R-MAT with scale ceil(log2(E/16)), E samples and
+    (a, b, c, d) each jittered uniformly by +-0.05 around RMAT_ABC (d kept
+    >= 0.01, renormalised), or with probability cl_share the grid +
+    diagonals + Chung-Lu overlay sized to about E pairs."""
+    import math
+    strata = list(range(count))
+    for i in range(count - 1, 0, -1):            # Fisher-Yates on the strata
+        j = int(gen_hash(seed, 30, i) % (i + 1))
+        strata[i], strata[j] = strata[j], strata[i]
+    specs = []
+    for i in range(count):
+        u = (strata[i] + _unit(seed, 31, i)) / count
+        e = int(round(e_min * (e_max / e_min) ** u))
+        if _unit(seed, 32, i) < cl_share:
+            side = max(4, int(round(math.sqrt(e / 4.05))))
+            specs.append(dict(kind="grid", side=side, pdiag=0.05, gamma=2.1, mean_deg=4.0,
+                              seed=seed + 1 + i, pairs=e))
+        else:
+            a, b, c = RMAT_ABC
+            w = [a, b, c, 1.0 - a - b - c]
+            w = [x + 0.1 * (_unit(seed, 33 + k, i) - 0.5) for k, x in enumerate(w)]
+            w[3] = max(w[3], 0.01)
+            tot = sum(w)
+            w = [x / tot for x in w]
+            scale = max(4, math.ceil(math.log2(e / 16)))
+            specs.append(dict(kind="rmat", scale=scale, samples=e, abc=(w[0], w[1], w[2]),
+                              seed=seed + 1 + i, pairs=e))
+    return specs
+
+
+def served_graph(spec: dict, threads: int | None = None):
+    """(src, dst, n) of one pool entry of served_pool_specs."""
+    if spec["kind"] == "rmat":
+        return rmat(spec["scale"], seed=spec["seed"], abc=spec["abc"], samples=spec["samples"],
+                    threads=threads)
+    return grid_chung_lu(spec["side"], spec["pdiag"], spec["gamma"], spec["mean_deg"], seed=spec["seed"],
+                         threads=threads)

@@ -300,6 +300,69 @@ tc_status tc_csr_centrality_noalloc(const int64_t* d_row_ptr, const int32_t* d_c
                                     int64_t nnz, uint64_t* d_tri, uint64_t* d_numer, double* d_tc,
                                     tc_stream stream);
 
+/*
+ * Serving: a request loop over the batch path (no counterpart in the
+ * paper; it serves a stream of independent graphs).  Callers submit graphs
+ * as host pair lists at any time; worker threads, each with its own
+ * stream, take the waiting requests in arrival order and run as many of
+ * them together as fit in one disjoint-union batch (up to max_batch_pairs
+ * pairs and within the device-memory budget left by the batches in
+ * flight), so requests that arrive while others run join the next batch.
+ * With several workers, one batch's copies and build overlap another's
+ * count and gather.  Each request gets exactly the results the same graph
+ * gets alone (tc_count and tc_centrality on it).
+ */
+typedef struct tc_server tc_server;   /* opaque */
+
+typedef struct {
+    int64_t id;           /* as returned by tc_server_submit                  */
+    int32_t status;       /* TC_OK, TC_NO_TRIANGLES or a negative tc_status   */
+    int32_t batch_size;   /* requests in the batch that served this one       */
+    uint64_t triangles;   /* △(G) of the request's graph                      */
+    int64_t edges;        /* m: undirected edges after de-duplication         */
+    double t_submit;      /* seconds since the server was created             */
+    double t_start;       /* its batch began (copies, build, count, gather)   */
+    double t_done;        /* its results were in the caller's buffers         */
+} tc_request_info;
+
+/*
+ * Starts `workers` (1..8) worker threads on the current device.
+ * memory_budget_bytes caps the device memory that running batches may
+ * hold, by an estimate of each request's peak use; max_batch_pairs caps
+ * the pairs of one batch (a larger single request still runs, alone).
+ */
+tc_status tc_server_create(int64_t memory_budget_bytes, int64_t max_batch_pairs, int workers,
+                           tc_server** out);
+
+/*
+ * Queues one graph: num_pairs int32 pairs (h_src[i], h_dst[i]) in [0, n),
+ * host memory (pinned memory moves fastest).  Results land in h_tri[n]
+ * (△(v)) and h_tc[n] (TC(v)), host memory, either may be NULL.  All four
+ * buffers must stay valid and untouched until the request is reported by
+ * tc_server_poll.  Returns TC_ERR_OUT_OF_MEMORY at once, without touching
+ * the device, when the request's own estimate exceeds the whole budget;
+ * TC_ERR_STATE once the server is shutting down.  Never blocks on the GPU.
+ */
+tc_status tc_server_submit(tc_server* srv, const int32_t* h_src, const int32_t* h_dst,
+                           int64_t num_pairs, int64_t n, uint64_t* h_tri, double* h_tc,
+                           int64_t* request_id);
+
+/*
+ * Moves up to `cap` finished requests into out[], *count of them; waits up
+ * to wait_ms milliseconds for the first one if none has finished.
+ */
+tc_status tc_server_poll(tc_server* srv, tc_request_info* out, int cap, int* count, int wait_ms);
+
+/* Batches run so far, requests waiting, requests running, budget in use. */
+tc_status tc_server_stats(tc_server* srv, int64_t* batches, int64_t* waiting, int64_t* running,
+                          int64_t* memory_in_use);
+
+/* Stops the server: batches already running finish (their result buffers
+ * are filled), requests still waiting are dropped without running, then
+ * the workers exit and the server is freed.  Poll until every request has
+ * been reported first to receive all results. */
+void tc_server_free(tc_server* srv);
+
 /* Releases g.  Its device memory is freed in stream order on the stream of
  * the last call made on g, which must still exist. */
 void tc_graph_free(tc_graph* g);

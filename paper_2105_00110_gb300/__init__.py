@@ -43,13 +43,20 @@ EXPORTED = ["tc_build_csr", "tc_count", "tc_centrality", "tc_divide", "tc_graph_
             "tc_profile_reset", "tc_profile_read", "tc_launch_count", "tc_graph_free",
             "tc_status_str", "tc_batch_build", "tc_batch_run", "tc_batch_info",
             "tc_batch_copy_edges", "tc_batch_get_stats", "tc_batch_autotune", "tc_batch_get_params",
-            "tc_batch_free", "tc_csr_centrality_noalloc"]
+            "tc_batch_free", "tc_csr_centrality_noalloc",
+            "tc_server_create", "tc_server_submit", "tc_server_poll", "tc_server_stats", "tc_server_free"]
 
 
 class TCError(RuntimeError):
     def __init__(self, status: int, where: str):
         super().__init__("%s failed: %s (%d)" % (where, status_str(status), status))
         self.status = status
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("batch_size", ctypes.c_int32),
+                ("triangles", ctypes.c_uint64), ("edges", ctypes.c_int64), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
 class GraphStats(ctypes.Structure):
@@ -137,6 +144,17 @@ def lib():
         L.tc_batch_get_params.argtypes = [vp, vp]
         L.tc_batch_free.restype = None
         L.tc_batch_free.argtypes = [vp]
+        L.tc_server_create.restype = i32
+        L.tc_server_create.argtypes = [i64, i64, i32, ctypes.POINTER(vp)]
+        L.tc_server_submit.restype = i32
+        L.tc_server_submit.argtypes = [vp, vp, vp, i64, i64, vp, vp, ctypes.POINTER(i64)]
+        L.tc_server_poll.restype = i32
+        L.tc_server_poll.argtypes = [vp, ctypes.POINTER(RequestInfo), i32, ctypes.POINTER(i32), i32]
+        L.tc_server_stats.restype = i32
+        L.tc_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                      ctypes.POINTER(i64)]
+        L.tc_server_free.restype = None
+        L.tc_server_free.argtypes = [vp]
         L.tc_csr_centrality_noalloc.restype = i32
         L.tc_csr_centrality_noalloc.argtypes = [vp, vp, i64, i64, vp, vp, vp, vp]
         _lib = L
@@ -443,3 +461,114 @@ class Batch:
         st = GraphStats()
         _check(lib().tc_batch_get_stats(self.h, ctypes.byref(st)), "tc_batch_get_stats", ok=(TC_OK,))
         return st.as_dict()
+
+
+# ----------------------------------------------------------------- serving
+def _host_ptr(a, dtype):
+    """Address of a contiguous host array (numpy or CPU torch) of `dtype`."""
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or not a.is_contiguous() or a.dtype != dtype[1]:
+            raise ValueError("expected a contiguous CPU tensor of %s" % dtype[1])
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or not a.flags.c_contiguous or a.dtype != dtype[0]:
+        raise ValueError("expected a C-contiguous numpy array of %s" % dtype[0])
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+_I32 = (np.dtype(np.int32), torch.int32)
+_U64 = (np.dtype(np.uint64), torch.uint64)
+_F64 = (np.dtype(np.float64), torch.float64)
+
+
+def tc_server_create(memory_budget_bytes: int, max_batch_pairs: int, workers: int = 2):
+    h = ctypes.c_void_p()
+    _check(lib().tc_server_create(int(memory_budget_bytes), int(max_batch_pairs), int(workers),
+                                  ctypes.byref(h)), "tc_server_create", ok=(TC_OK,))
+    return h
+
+
+def tc_server_submit(srv, src, dst, n: int, tri=None, tc=None) -> int:
+    rid = ctypes.c_int64()
+    st = lib().tc_server_submit(srv, _host_ptr(src, _I32), _host_ptr(dst, _I32), len(src), int(n),
+                                _host_ptr(tri, _U64), _host_ptr(tc, _F64), ctypes.byref(rid))
+    _check(st, "tc_server_submit", ok=(TC_OK,))
+    return rid.value
+
+
+def tc_server_poll(srv, cap: int = 1024, wait_ms: int = 0, buf=None):
+    if buf is None or len(buf) < cap:
+        buf = (RequestInfo * max(cap, 1))()
+    cnt = ctypes.c_int32()
+    _check(lib().tc_server_poll(srv, buf, int(cap), ctypes.byref(cnt), int(wait_ms)), "tc_server_poll",
+           ok=(TC_OK,))
+    return [dict(id=r.id, status=r.status, batch_size=r.batch_size, triangles=r.triangles, edges=r.edges,
+                 t_submit=r.t_submit, t_start=r.t_start, t_done=r.t_done) for r in buf[:cnt.value]]
+
+
+def tc_server_stats(srv) -> dict:
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().tc_server_stats(srv, *(ctypes.byref(x) for x in v)), "tc_server_stats", ok=(TC_OK,))
+    return dict(batches=v[0].value, waiting=v[1].value, running=v[2].value, memory_in_use=v[3].value)
+
+
+def tc_server_free(srv):
+    lib().tc_server_free(srv)
+
+
+class Server:
+    """Request loop on the current device.  submit() takes host int32 pair
+    arrays and returns a request id at once; poll() returns finished
+    requests with their results.  The arrays of a request are kept alive
+    here until it has been polled."""
+
+    def __init__(self, memory_budget_bytes: int = 150 * 10**9, max_batch_pairs: int = 1 << 25,
+                 workers: int = 2):
+        self.h = None
+        self.h = tc_server_create(memory_budget_bytes, max_batch_pairs, workers)
+        self.live = {}
+        self._buf = None
+
+    def submit(self, src, dst, n: int, tri=None, tc=None, want_results: bool = True) -> int:
+        if want_results and tri is None:
+            tri = np.empty(max(int(n), 1), np.uint64)
+        if want_results and tc is None:
+            tc = np.empty(max(int(n), 1), np.float64)
+        rid = tc_server_submit(self.h, src, dst, n, tri, tc)
+        self.live[rid] = (src, dst, tri, tc, int(n))
+        return rid
+
+    def poll(self, cap: int = 4096, wait_ms: int = 0):
+        if self._buf is None or len(self._buf) < cap:
+            self._buf = (RequestInfo * max(cap, 1))()
+        out = []
+        for info in tc_server_poll(self.h, cap, wait_ms, self._buf):
+            src, dst, tri, tc, n = self.live.pop(info["id"])
+            info["tri"] = None if tri is None else tri[:n]
+            info["tc"] = None if tc is None else tc[:n]
+            out.append(info)
+        return out
+
+    def wait_all(self, timeout_s: float = 600.0):
+        import time as _t
+        done = []
+        t_end = _t.monotonic() + timeout_s
+        while self.live and _t.monotonic() < t_end:
+            done += self.poll(wait_ms=100)
+        return done
+
+    def stats(self) -> dict:
+        return tc_server_stats(self.h)
+
+    def close(self):
+        if self.h:
+            tc_server_free(self.h)
+            self.h = None
+            self.live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtc_gb300.so")
-SOURCES = ["tc_api.cu", "tc_build.cu", "tc_count.cu", "tc_gather.cu", "tc_batch.cu", "tc_noalloc.cu"]
+SOURCES = ["tc_api.cu", "tc_build.cu", "tc_count.cu", "tc_gather.cu", "tc_batch.cu", "tc_noalloc.cu", "tc_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
