@@ -64,6 +64,47 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# ------------------------------------------------------- DRAM traffic
+COUNT_SOURCES = ["paper_2105_00110_gb300/csrc/tc_count.cu", "paper_2105_00110_gb300/csrc/tc_internal.cuh"]
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "count_dram_traffic_rmat24.md")
+
+
+def count_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in COUNT_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def dram_traffic(kernel: str, workload: str):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of `kernel`
+    from the committed ncu summary, or None when that summary is for other
+    count-kernel sources or another workload."""
+    try:
+        with open(TRAFFIC_PROFILE) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    sha = wl = None
+    rows = {}
+    for line in text.splitlines():
+        if line.startswith("source-sha256:"):
+            sha = line.split(":", 1)[1].strip()
+        elif line.startswith("workload:"):
+            wl = line.split(":", 1)[1].strip()
+        elif line.startswith("| count_") or line.startswith("| gather"):
+            cells = [c.strip() for c in line.strip("|").split("|")]
+            try:
+                rows[cells[0]] = (float(cells[1]) + float(cells[2])) * 1e9
+            except (ValueError, IndexError):
+                pass
+    if sha != count_sources_sha() or wl != workload:
+        return None
+    return rows.get(kernel)
+
+
 # --------------------------------------------------------------- clocks
 class ClockSampler:
     QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -252,7 +293,7 @@ def run_ours(args, spec, wl_name):
             achieved = bytes_per[name] / avg_s / 1e9
             roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1),
                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "frac": round(achieved / peak, 4), "traffic": dram_traffic(name, wl_name),
                     "algorithmic_bytes_per_launch": bytes_per[name],
                     "avg_launch_ms": round(tot_ms / launch_n, 4)}
         step_ms = t_max / args.steps
@@ -614,7 +655,7 @@ def run_served(args, spec, wl_name):
 
 
 # ------------------------------------------------------------- oracle side
-CPU_SAMPLE = dict(kind="rmat", scale=18, edge_factor=16, seed=0x5EED0012)
+CPU_SAMPLE = dict(kind="rmat", scale=20, edge_factor=16, seed=0x5EED0012)
 
 
 def oracle_pass(spec):
@@ -630,7 +671,7 @@ def oracle_pass(spec):
 def cpu_baseline(args):
     m, dt = oracle_pass(CPU_SAMPLE)
     return {"value": m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": "R-MAT scale 18, edge factor 16, same (a,b,c,d), full TC by the oracle "
+            "sample": "R-MAT scale 20, edge factor 16, same (a,b,c,d), full TC by the oracle "
                       "(canonical CSR, degree-ordered listing, Definition 1 numerators, exact "
                       "division), single thread, %.1f s" % dt}
 

@@ -42,6 +42,9 @@ typedef unsigned long long ull;
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kCtaWarps = TC_CTA_THREADS / 32;
+#ifndef TC_PRED_WORD
+#define TC_PRED_WORD 0
+#endif
 #ifndef TC_CTA_MIN_BLOCKS
 #define TC_CTA_MIN_BLOCKS 4   // CTAs per SM the CTA-item kernels are compiled for
 #endif
@@ -291,6 +294,17 @@ __device__ __forceinline__ uint32_t visit_octet<lookup_bitmap, true>(const looku
                                                                     ull* __restrict__ tri,
                                                                     uint32_t* __restrict__ flag) {
     uint32_t word[8], boff[8];
+#if TC_PRED_WORD
+    // slots outside [0, len) (alignment padding) issue no shared load
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        boff[k] = min((uint32_t)(o.x[k] - lk.base), (uint32_t)lk.nbits);
+        word[k] = (unsigned)(off + k) < (unsigned)len ? lk.bits[boff[k] >> 5] : 0u;
+    }
+    uint32_t hm = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) hm |= ((word[k] >> (boff[k] & 31)) & 1u) << k;
+#else
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         boff[k] = min((uint32_t)(o.x[k] - lk.base), (uint32_t)lk.nbits);
@@ -300,6 +314,7 @@ __device__ __forceinline__ uint32_t visit_octet<lookup_bitmap, true>(const looku
 #pragma unroll
     for (int k = 0; k < 8; ++k)
         hm |= (((word[k] >> (boff[k] & 31)) & 1u) & ((unsigned)(off + k) < (unsigned)len ? 1u : 0u)) << k;
+#endif
     if (hm == 0) return 0;
     int l[8];
 #pragma unroll
@@ -741,15 +756,25 @@ inline int blocks_for(int64_t items) {
 }
 
 // Per-kernel launch shape, computed once (so that later launches, e.g.
-// inside a stream capture, make no attribute or occupancy calls).
+// inside a stream capture, make no attribute or occupancy calls).  One
+// kernel may be launched with several dynamic shared sizes (the bitmap
+// kernel serves both bitmap classes), and its maximum-dynamic-shared
+// attribute is one value per kernel: it is only ever raised, so a launch
+// with a smaller size never lowers it below what a larger one needs.
 struct launch_shape {
     const void* fn;
     size_t smem;
     int per_sm;
 };
+struct smem_attr {
+    const void* fn;
+    size_t max_smem;
+};
 std::mutex g_shape_mu;
 launch_shape g_shapes[32];
 int g_nshapes = 0;
+smem_attr g_attrs[16];
+int g_nattrs = 0;
 
 tc_status shape_for(const void* fn, size_t smem, int& per_sm) {
     std::lock_guard<std::mutex> lk(g_shape_mu);
@@ -759,7 +784,15 @@ tc_status shape_for(const void* fn, size_t smem, int& per_sm) {
             return TC_OK;
         }
     // static + dynamic shared memory may exceed the 48 KB default
-    if (smem > 0) TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 0) {
+        int a = 0;
+        while (a < g_nattrs && g_attrs[a].fn != fn) ++a;
+        if (a == g_nattrs || g_attrs[a].max_smem < smem) {
+            TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            if (a == g_nattrs && g_nattrs < 16) g_attrs[g_nattrs++] = smem_attr{fn, smem};
+            else if (a < g_nattrs) g_attrs[a].max_smem = smem;
+        }
+    }
     TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TC_CTA_THREADS, smem));
     per_sm = std::max(per_sm, 1);
     if (g_nshapes < 32) g_shapes[g_nshapes++] = launch_shape{fn, smem, per_sm};

@@ -127,6 +127,30 @@ def test_rmat16_many_tiles(strategy):
         assert items[3] == sum(items)
 
 
+def test_both_bitmap_classes_repeatedly():
+    # the bitmap kernel runs with two dynamic shared sizes (small and large
+    # windows); alternating them across calls must keep every launch valid
+    s, d, n = gg.rmat(21, seed=0x5EED0015)
+    g = tcg.Graph(torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), n)
+    g.set_strategy("bitmap")                   # every window that fits 100 KB is a bitmap
+    runs = []
+    for it in range(3):
+        tri, flags, total, _ = g.count()
+        numer, tcv, den, _ = g.centrality()
+        torch.cuda.synchronize()
+        runs.append((tri.cpu().numpy(), flags.cpu().numpy(), total, tcv.cpu().numpy().view(np.int64)))
+        if it == 0:
+            items = g.stats()["items"]
+            assert items[0] > 0 and items[1] > 0
+    g.close()
+    ref = gpu_run(s, d, n, strategy="merge")    # no bitmap at all
+    for tri, flags, total, tcb in runs:
+        assert total == ref["total"]
+        np.testing.assert_array_equal(tri, ref["tri"])
+        np.testing.assert_array_equal(flags, ref["flag"])
+        np.testing.assert_array_equal(tcb, ref["tc"].view(np.int64))
+
+
 def test_grid_chung_lu_small():
     for strategy in STRATS:
         check(*gg.grid_chung_lu(side=96, seed=0x5EED0002), strategy=strategy)
