@@ -655,7 +655,7 @@ def run_served(args, spec, wl_name):
 
 
 # ------------------------------------------------------------- oracle side
-CPU_SAMPLE = dict(kind="rmat", scale=20, edge_factor=16, seed=0x5EED0012)
+CPU_SAMPLE = dict(kind="rmat", scale=19, edge_factor=16, seed=0x5EED0012)
 
 
 def oracle_pass(spec):
@@ -671,7 +671,7 @@ def oracle_pass(spec):
 def cpu_baseline(args):
     m, dt = oracle_pass(CPU_SAMPLE)
     return {"value": m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": "R-MAT scale 20, edge factor 16, same (a,b,c,d), full TC by the oracle "
+            "sample": "R-MAT scale 19, edge factor 16, same (a,b,c,d), full TC by the oracle "
                       "(canonical CSR, degree-ordered listing, Definition 1 numerators, exact "
                       "division), single thread, %.1f s" % dt}
 

@@ -42,36 +42,36 @@ typedef unsigned long long ull;
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kCtaWarps = TC_CTA_THREADS / 32;
-#ifndef TC_PRED_WORD
-#define TC_PRED_WORD 0
-#endif
 #ifndef TC_CTA_MIN_BLOCKS
 #define TC_CTA_MIN_BLOCKS 4   // CTAs per SM the CTA-item kernels are compiled for
 #endif
 
 // Planner constants.
-constexpr int64_t kBitmapSmallSmem = 32 * 1024;   // dynamic smem of the small-bitmap CTA kernel (5 CTAs per SM)
+// 40 KB keeps four CTAs per SM (the register limit) with room left for L1
+constexpr int64_t kBitmapSmallSmem = 40 * 1024;   // dynamic smem of the small-bitmap CTA kernel
 constexpr int64_t kBitmapLargeSmem = 100 * 1024;  // ... of the large-bitmap CTA kernel
 constexpr int64_t kCtaListSmem = 100 * 1024;      // ... of the CTA sorted-list kernel
 
 enum { L_BITMAP = 0, L_SORTED = 1, L_GLOBAL = 2 };
 
 // ------------------------------------------------------------ lookups
-// N_H(v) as a bitmap over [base, base + nbits): bit (w - base) set iff
-// w ∈ N_H(v); rank[k] = set bits before word k (16 bits suffice since
-// |N_H(v)| <= sqrt(2m) < 2^16) gives w's staged index.  Bit nbits is
-// always clear (a zero guard word follows the window), so an id outside the
-// window is clamped onto it and the test needs no branch.
+// N_H(v) as a bitmap over the id window [base, base + nbits), base = v + 1,
+// in 32-bit entries of 16 ids each: the low half holds the membership bits
+// of ids [16 i, 16 i + 16) of the window, the high half the number of
+// members before them (16 bits suffice since |N_H(v)| <= sqrt(2m) < 2^16).
+// One shared load answers both "is w in N_H(v)" and "at which staged index".
+// The offset nbits is never a member (the entry after the window is a zero
+// guard), so an id outside the window is clamped onto it and the test
+// needs no branch.
 struct lookup_bitmap {
-    const uint32_t* bits;
-    const uint16_t* rank;
+    const uint32_t* bits;   // the entries
     int32_t base;
     int32_t nbits;
     __device__ __forceinline__ bool find(int32_t w, int& l) const {
         const uint32_t off = min((uint32_t)(w - base), (uint32_t)nbits);
-        const uint32_t word = bits[off >> 5];
-        if (!((word >> (off & 31)) & 1u)) return false;
-        l = (int)rank[off >> 5] + __popc(word & ((1u << (off & 31)) - 1));
+        const uint32_t e = bits[off >> 4];
+        if (!((e >> (off & 15)) & 1u)) return false;
+        l = (int)(e >> 16) + __popc(e & ((1u << (off & 15)) - 1));
         return true;
     }
 };
@@ -116,9 +116,10 @@ struct lookup_global {
     }
 };
 
-// Shared bytes of a bitmap staging: bits, 16-bit ranks, per-id counters.
+// Shared bytes of a bitmap staging: 16-id entries (+ guard, padded to even)
+// and per-id counters; `words` is the window in 32-id units.
 __host__ __device__ __forceinline__ int64_t bitmap_bytes(int64_t words, int64_t hv) {
-    return 4 * (words + 1) + 2 * ((words + 2) & ~1ll) + 4 * hv;   // + one zero guard word
+    return 4 * (2 * words + 2) + 4 * hv;
 }
 
 __device__ __forceinline__ ull warp_sum(ull x) {
@@ -133,25 +134,24 @@ __device__ __forceinline__ lookup_bitmap build_bitmap(int t, int nt, uint8_t* re
                                                       const int32_t* __restrict__ col,
                                                       uint32_t*& cnt, Barrier barrier,
                                                       uint32_t* scan_tmp, int lane, int warp, int nwarps) {
-    const int words = (nbits + 31) >> 5;
-    uint32_t* bits = (uint32_t*)region;                     // words + 1 (guard)
-    uint16_t* rank = (uint16_t*)(bits + words + 1);         // words + 1, padded to even
-    cnt = (uint32_t*)(rank + ((words + 2) & ~1));
+    // entry i: membership bits of ids [16 i, 16 i + 16) of the window in its
+    // low half, the members before it in its high half
+    const int ents = (nbits + 15) >> 4;
+    uint32_t* ent = (uint32_t*)region;                      // ents + 1 (guard)
+    cnt = ent + ((ents + 2) & ~1);
     const int32_t base = v + 1;
-    for (int i = t; i <= words; i += nt) bits[i] = 0;
+    for (int i = t; i <= ents; i += nt) ent[i] = 0;
     for (int i = t; i < hv; i += nt) cnt[i] = 0;
     barrier();
     for (int i = t; i < hv; i += nt) {
         const int32_t off = col[h0 + i] - base;
-        atomicOr(&bits[off >> 5], 1u << (off & 31));
+        atomicOr(&ent[off >> 4], 1u << (off & 15));
     }
     barrier();
-    // rank: per-thread contiguous slices, a warp scan of the slice sums and,
-    // for more than one warp, a scan over the warp totals
-    const int per = (words + nt - 1) / nt;
-    const int w0 = min(t * per, words), w1 = min(w0 + per, words);
+    const int per = (ents + nt - 1) / nt;
+    const int e0 = min(t * per, ents), e1 = min(e0 + per, ents);
     uint32_t sum = 0;
-    for (int i = w0; i < w1; ++i) sum += __popc(bits[i]);
+    for (int i = e0; i < e1; ++i) sum += __popc(ent[i]);
     uint32_t incl = sum;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -165,13 +165,13 @@ __device__ __forceinline__ lookup_bitmap build_bitmap(int t, int nt, uint8_t* re
         for (int k = 0; k < warp; ++k) before += scan_tmp[k];
     }
     uint32_t run = before + incl - sum;
-    for (int i = w0; i < w1; ++i) {
-        rank[i] = (uint16_t)run;
-        run += __popc(bits[i]);
+    for (int i = e0; i < e1; ++i) {
+        const uint32_t x = ent[i];
+        ent[i] = x | (run << 16);
+        run += __popc(x);
     }
-    if (t == nt - 1) rank[words] = (uint16_t)(before + incl);   // guard word
     barrier();
-    return lookup_bitmap{bits, rank, base, nbits};
+    return lookup_bitmap{ent, base, nbits};
 }
 
 // ------------------------------------------------------------ streams
@@ -284,9 +284,10 @@ __device__ __forceinline__ uint32_t visit_octet(const LK& lk, const octet& o, in
     return nh;
 }
 
-// The bitmap form in explicit phases — the 8 word loads, the hit mask, the
-// rank loads of the hits, then the counter atomics — so that the loads of
-// an octet overlap instead of each waiting behind the previous id's atomic.
+// The bitmap form in explicit phases — the 8 entry loads, the hit mask, the
+// staged indices of the hits, then the counter atomics — so that the loads
+// of an octet overlap instead of each waiting behind the previous id's
+// atomic.
 template <>
 __device__ __forceinline__ uint32_t visit_octet<lookup_bitmap, true>(const lookup_bitmap& lk, const octet& o,
                                                                     int64_t pos, int off, int len,
@@ -294,32 +295,20 @@ __device__ __forceinline__ uint32_t visit_octet<lookup_bitmap, true>(const looku
                                                                     ull* __restrict__ tri,
                                                                     uint32_t* __restrict__ flag) {
     uint32_t word[8], boff[8];
-#if TC_PRED_WORD
-    // slots outside [0, len) (alignment padding) issue no shared load
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         boff[k] = min((uint32_t)(o.x[k] - lk.base), (uint32_t)lk.nbits);
-        word[k] = (unsigned)(off + k) < (unsigned)len ? lk.bits[boff[k] >> 5] : 0u;
-    }
-    uint32_t hm = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) hm |= ((word[k] >> (boff[k] & 31)) & 1u) << k;
-#else
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        boff[k] = min((uint32_t)(o.x[k] - lk.base), (uint32_t)lk.nbits);
-        word[k] = lk.bits[boff[k] >> 5];
+        word[k] = lk.bits[boff[k] >> 4];
     }
     uint32_t hm = 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-        hm |= (((word[k] >> (boff[k] & 31)) & 1u) & ((unsigned)(off + k) < (unsigned)len ? 1u : 0u)) << k;
-#endif
+        hm |= (((word[k] >> (boff[k] & 15)) & 1u) & ((unsigned)(off + k) < (unsigned)len ? 1u : 0u)) << k;
     if (hm == 0) return 0;
     int l[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-        l[k] = (hm >> k) & 1u ? (int)lk.rank[boff[k] >> 5] + __popc(word[k] & ((1u << (boff[k] & 31)) - 1)) : 0;
+        l[k] = (hm >> k) & 1u ? (int)(word[k] >> 16) + __popc(word[k] & ((1u << (boff[k] & 15)) - 1)) : 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k)
         if ((hm >> k) & 1u) atomicAdd(&cnt[l[k]], 1u);
@@ -455,7 +444,7 @@ __device__ __forceinline__ int compact_warp(int lane, const entry& e, stream_tab
 #define TC_WARP_G 1
 #endif
 #ifndef TC_CTA_G
-#define TC_CTA_G 2
+#define TC_CTA_G 3
 #endif
 constexpr int kWarpG = TC_WARP_G;   // octets (8 ids) per lane per window, warp items
 constexpr int kCtaG = TC_CTA_G;     // octets per lane per window, CTA items
