@@ -5,14 +5,17 @@
 //     (the set-up of section "Comparison": symmetrised, loop-free, simple)
 //  2. radix sort + unique -> the m undirected edges, caller labels
 //  3. degrees; π = sort by (degree, label) (section "Notation")
-//  4. both directions of every edge relabelled by π, radix sorted ->
-//     symmetric CSR in rank space, rows ascending, so each row is
-//     [N_L(v) | N_H(v)] (Lemma 1's partition, done by sorting)
-//  5. hstart (row split), edge_tail, twin and hrem of every head entry
+//  4. every edge relabelled by π and placed in the run of its lower end;
+//     each run sorted (warp registers, a warp's shared region or a CTA,
+//     by length) -> symmetric CSR in rank space whose rows are
+//     [N_L(v) | N_H(v)] (Lemma 1's partition), N_H(v) ascending
+//  5. written with the runs: col, edge_tail, and the head record
+//     {u, hrem, twin} of every lower neighbour
 //  6. planner: per middle vertex v its work W(v) = Σ_{u∈N_L(v)} hrem, and
 //     the work items of the count step, heavy vertices split into chunks
 //
-// Radix sorts and scans use CUB (header-only, compiled into this library).
+// Radix sorts (steps 2-3) and scans use CUB (header-only, compiled into
+// this library); the per-row run sorts are this file's own.
 #include <cub/cub.cuh>
 
 #include <algorithm>
@@ -91,49 +94,210 @@ __global__ void k_rank_apply(const uint64_t* __restrict__ sorted, int64_t n, int
 }
 
 // Every undirected edge once in rank space: key (lo, hi) with lo < hi the
-// ranks of its ends, value its canonical id; d_H(lo) counted.
+// ranks of its ends, at its canonical id; d_H(lo) counted.
 __global__ void k_edge_rank_keys(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
                                  const int32_t* __restrict__ rank, int64_t m, int bits,
-                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                 int32_t* __restrict__ dh) {
+                                 uint64_t* __restrict__ keys, int32_t* __restrict__ dh) {
     GRID_STRIDE(e, m) {
         const uint64_t ru = (uint64_t)rank[eu[e]], rv = (uint64_t)rank[ev[e]];
         const uint64_t lo = ru < rv ? ru : rv, hi = ru < rv ? rv : ru;
         keys[e] = (lo << bits) | hi;
-        vals[e] = (uint32_t)e;
         atomicAdd(&dh[lo], 1);
     }
 }
 
-// Row split: the last d_H(r) entries of row r hold N_H(r).
-__global__ void k_hstart(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ dh, int64_t n,
-                         int64_t* __restrict__ hstart) {
-    GRID_STRIDE(r, n) hstart[r] = row_ptr[r + 1] - dh[r];
+// Row split: the last d_H(r) entries of row r hold N_H(r).  The head cursor
+// of row r starts at its first entry (an absolute CSR position), its
+// tail-run cursor at hptr[r] (the run's start in the compact tail order).
+template <class C>
+__global__ void k_hstart(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ dh,
+                         const int64_t* __restrict__ hptr, int64_t n, int64_t* __restrict__ hstart,
+                         C* __restrict__ hnext, C* __restrict__ tnext) {
+    GRID_STRIDE(r, n) {
+        hstart[r] = row_ptr[r + 1] - dh[r];
+        hnext[r] = (C)row_ptr[r];
+        tnext[r] = (C)hptr[r];
+    }
 }
 
-// Writes both entries of every edge.  The edges arrive sorted by (lo, hi),
-// so the tail entry (row lo, N_H(lo) ascending) of the i-th edge is at
-// hstart[lo] + (i - hptr[lo]); the head entry (row hi, N_L(hi) in any
-// order) takes the next free slot of row hi's head as the record
-// {lo, |{w ∈ N_H(lo) : w > hi}|, tail position}.
-__global__ void k_scatter(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t m,
-                          int bits, const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
-                          const int64_t* __restrict__ hptr, int32_t* __restrict__ hcur,
-                          int32_t* __restrict__ col, tc_head* __restrict__ head,
-                          int64_t* __restrict__ edge_tail) {
+// Each edge to the next free slot of its lower end's run (row r's run
+// starts at hptr[r]) as (hi << 32) | edge id, so that sorting each run puts
+// N_H(lo) in order with the edge ids alongside.
+template <class C>
+__global__ void k_tail_place(const uint64_t* __restrict__ keys, int64_t m, int bits, C* __restrict__ tnext,
+                             uint64_t* __restrict__ slot) {
     const uint64_t mask = (1ull << bits) - 1;
-    GRID_STRIDE(i, m) {
-        const uint64_t k = keys[i];
-        const int64_t lo = (int64_t)(k >> bits), hi = (int64_t)(k & mask);
-        const int64_t tail = hstart[lo] + (i - hptr[lo]);
-        col[tail] = (int32_t)hi;
-        edge_tail[vals[i]] = tail;
-        const int64_t hp = row_ptr[hi] + atomicAdd(&hcur[hi], 1);
-        tc_head rec;
-        rec.u = (int32_t)lo;
-        rec.hrem = (int32_t)(row_ptr[lo + 1] - tail - 1);
-        rec.twin = tail;
-        head[hp] = rec;   // one 16-byte store
+    GRID_STRIDE(e, m) {
+        const uint64_t k = keys[e];
+        const uint64_t lo = k >> bits, hi = k & mask;
+        const int64_t i = (int64_t)atomicAdd(&tnext[lo], (C)1);
+        slot[i] = (hi << 32) | (uint64_t)e;
+    }
+}
+
+// Both entries of one edge, from the i-th element x of row r's sorted run
+// (tail position t = hstart[r] + i): the tail entry col[t] = hi, the edge's
+// canonical id -> t, and the head entry in row hi (N_L(hi) in any order) at
+// the next free slot of its cursor, as the record
+// {r, |{w ∈ N_H(r) : w > hi}| = e - t - 1, twin = t}.
+template <class C>
+__device__ __forceinline__ void emit_tail(int64_t r, int64_t t, int64_t e, uint64_t x, C* __restrict__ hnext,
+                                          int32_t* __restrict__ col, tc_head* __restrict__ head,
+                                          int64_t* __restrict__ edge_tail) {
+    const int32_t hi = (int32_t)(x >> 32);
+    col[t] = hi;
+    edge_tail[x & 0xffffffffull] = t;
+    const int64_t hp = (int64_t)atomicAdd(&hnext[hi], (C)1);
+    tc_head rec;
+    rec.u = (int32_t)r;
+    rec.hrem = (int32_t)(e - t - 1);
+    rec.twin = t;
+    head[hp] = rec;   // one 16-byte store
+}
+
+// Every run is sorted by bitonic merges in the form whose compare-exchanges
+// all put the smaller key at the lower index: the first step of the k-merge
+// pairs i with its mirror in the k-block (i ^ (k - 1)), the later steps pair
+// i with i ^ j.  A run of length L sorts as if padded with +inf up to a
+// power of two, since every pair whose upper index is >= L is a no-op; no
+// padding is stored.
+__device__ __forceinline__ uint64_t shfl_xor64(uint64_t x, int m) {
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)x, m);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(x >> 32), m);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// One step (merge k, distance j) of the network over key[0, len), padded to
+// P, by the threads t0, t0 + nt, ... of a team.
+__device__ __forceinline__ void run_network_step(uint64_t* key, int len, int P, int k, int j, int t0, int nt) {
+    const int lj = __ffs(j) - 1;
+    for (int t = t0; t < (P >> 1); t += nt) {
+        const int a = ((t >> lj) << (lj + 1)) | (t & (j - 1));
+        const int b = j == (k >> 1) ? a ^ (k - 1) : a | j;
+        if (b < len) {
+            const uint64_t xa = key[a], xb = key[b];
+            if (xb < xa) {
+                key[a] = xb;
+                key[b] = xa;
+            }
+        }
+    }
+}
+
+// Runs of 1..32 tails.  A warp takes 32 rows at a time, one per lane:
+// single-tail rows are written at once, runs of 2..32 are sorted one after
+// the other across the warp's registers (keys in lanes 0..L-1, +inf above),
+// longer runs are queued for k_runs_mid / k_runs_big.
+template <class C>
+__global__ void k_runs_small(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
+                             const int64_t* __restrict__ hptr, const uint64_t* __restrict__ slot, int64_t n,
+                             C* __restrict__ hnext, int32_t* __restrict__ col, tc_head* __restrict__ head,
+                             int64_t* __restrict__ edge_tail, int32_t* __restrict__ big,
+                             unsigned int* __restrict__ nbig) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; base < n;
+         base += warps * 32) {
+        const int64_t r = base + lane;
+        int64_t L = 0;
+        if (r < n) {
+            L = hptr[r + 1] - hptr[r];
+            if (L == 1) emit_tail(r, hstart[r], row_ptr[r + 1], slot[hptr[r]], hnext, col, head, edge_tail);
+            else if (L > 32) big[atomicAdd(nbig, 1u)] = (int32_t)r;
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, L >= 2 && L <= 32);
+        while (todo) {
+            const int j = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t rr = base + j;
+            const int64_t i0 = hptr[rr];
+            const int len = (int)(hptr[rr + 1] - i0);
+            uint64_t x = lane < len ? slot[i0 + lane] : ~0ull;
+#pragma unroll
+            for (int k = 2; k <= 32; k <<= 1) {
+                const uint64_t y = shfl_xor64(x, k - 1);   // mirror step
+                const bool low = (lane & (k - 1)) < (k >> 1);
+                x = low ? (x < y ? x : y) : (x < y ? y : x);
+#pragma unroll
+                for (int jj = k >> 2; jj > 0; jj >>= 1) {
+                    const uint64_t z = shfl_xor64(x, jj);
+                    const bool lo2 = (lane & jj) == 0;
+                    x = lo2 ? (x < z ? x : z) : (x < z ? z : x);
+                }
+            }
+            if (lane < len) emit_tail(rr, hstart[rr] + lane, row_ptr[rr + 1], x, hnext, col, head, edge_tail);
+        }
+    }
+}
+
+// Queued runs of 33..kMidRun tails: one warp per run, the network in the
+// warp's own shared region.
+constexpr int kMidRun = 1024;
+constexpr int kMidWarps = 4;
+
+template <class C>
+__global__ void __launch_bounds__(32 * kMidWarps)
+k_runs_mid(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
+           const int64_t* __restrict__ hptr, const uint64_t* __restrict__ slot, const int32_t* __restrict__ big,
+           const unsigned int* __restrict__ nbig, C* __restrict__ hnext, int32_t* __restrict__ col,
+           tc_head* __restrict__ head, int64_t* __restrict__ edge_tail) {
+    __shared__ uint64_t sk[kMidWarps][kMidRun];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint64_t* key = sk[w];
+    const unsigned count = *nbig;
+    const unsigned warps = gridDim.x * kMidWarps;
+    for (unsigned q = blockIdx.x * kMidWarps + w; q < count; q += warps) {
+        const int64_t r = big[q];
+        const int64_t i0 = hptr[r];
+        const int len = (int)(hptr[r + 1] - i0);
+        if (len > kMidRun) continue;
+        for (int i = lane; i < len; i += 32) key[i] = slot[i0 + i];
+        __syncwarp();
+        int P = 1;
+        while (P < len) P <<= 1;
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                run_network_step(key, len, P, k, j, lane, 32);
+                __syncwarp();
+            }
+        const int64_t h = hstart[r], e = row_ptr[r + 1];
+        for (int i = lane; i < len; i += 32) emit_tail(r, h + i, e, key[i], hnext, col, head, edge_tail);
+        __syncwarp();
+    }
+}
+
+// Queued runs longer than kMidRun: one CTA per run, the network in shared
+// memory (up to kRunSmem keys) or in place in `slot`.
+constexpr int kRunSmem = 4096;
+constexpr int kRunThreads = 512;
+
+template <class C>
+__global__ void __launch_bounds__(kRunThreads)
+k_runs_big(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
+           const int64_t* __restrict__ hptr, uint64_t* __restrict__ slot, const int32_t* __restrict__ big,
+           const unsigned int* __restrict__ nbig, C* __restrict__ hnext, int32_t* __restrict__ col,
+           tc_head* __restrict__ head, int64_t* __restrict__ edge_tail) {
+    __shared__ uint64_t sk[kRunSmem];
+    const unsigned count = *nbig;
+    for (unsigned q = blockIdx.x; q < count; q += gridDim.x) {
+        const int64_t r = big[q];
+        const int64_t i0 = hptr[r];
+        const int len = (int)(hptr[r + 1] - i0);
+        if (len <= kMidRun) continue;   // the same for every thread of the CTA
+        uint64_t* key = len <= kRunSmem ? sk : slot + i0;
+        if (len <= kRunSmem)
+            for (int i = threadIdx.x; i < len; i += blockDim.x) sk[i] = slot[i0 + i];
+        __syncthreads();
+        int P = 1;
+        while (P < len) P <<= 1;
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                run_network_step(key, len, P, k, j, threadIdx.x, blockDim.x);
+                __syncthreads();
+            }
+        const int64_t h = hstart[r], e = row_ptr[r + 1];
+        for (int i = threadIdx.x; i < len; i += blockDim.x) emit_tail(r, h + i, e, key[i], hnext, col, head, edge_tail);
+        __syncthreads();
     }
 }
 
@@ -155,36 +319,77 @@ struct row_stats {
     unsigned long long sum_h2, wedges, sum_dh, max_h, max_d;
 };
 
-// One warp per row: W(v) = Σ_{u ∈ N_L(v)} hrem(u, v), the number of ids the
-// count step streams for middle vertex v; plus shape statistics.
-__global__ void k_row_work(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
-                           const tc_head* __restrict__ head, int64_t n, int64_t* __restrict__ work,
-                           row_stats* __restrict__ st) {
+// W(v) = Σ_{u ∈ N_L(v)} hrem(u, v), the number of ids the count step
+// streams for middle vertex v, plus shape statistics.  Rows ascend in
+// degree: rows below band[0] (degree <= 32) take one thread each, the rest
+// one warp each.
+struct row_acc {
+    unsigned long long h2 = 0, w = 0, dh = 0, maxh = 0, maxd = 0;
+    __device__ __forceinline__ void add(unsigned long long hv, unsigned long long d, unsigned long long wr) {
+        h2 += hv * hv;
+        w += wr;
+        dh += d * hv;
+        maxh = maxh > hv ? maxh : hv;
+        maxd = maxd > d ? maxd : d;
+    }
+    __device__ __forceinline__ void flush(row_stats* st) {
+        for (int o = 16; o; o >>= 1) {
+            h2 += __shfl_xor_sync(0xffffffffu, h2, o);
+            w += __shfl_xor_sync(0xffffffffu, w, o);
+            dh += __shfl_xor_sync(0xffffffffu, dh, o);
+            const unsigned long long a = __shfl_xor_sync(0xffffffffu, maxh, o);
+            const unsigned long long c = __shfl_xor_sync(0xffffffffu, maxd, o);
+            maxh = maxh > a ? maxh : a;
+            maxd = maxd > c ? maxd : c;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&st->sum_h2, h2);
+            atomicAdd(&st->wedges, w);
+            atomicAdd(&st->sum_dh, dh);
+            atomicMax(&st->max_h, maxh);
+            atomicMax(&st->max_d, maxd);
+        }
+    }
+};
+
+__global__ void k_row_work_thread(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
+                                  const tc_head* __restrict__ head, const int64_t* __restrict__ band,
+                                  int64_t* __restrict__ work, row_stats* __restrict__ st) {
+    const int64_t r1 = band[0];
+    row_acc acc;
+    // whole warps step together so that the final shuffles see every lane
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t warp_first = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll;
+    for (int64_t base = warp_first; base < r1; base += stride) {
+        const int64_t r = base + (threadIdx.x & 31);
+        if (r < r1) {
+            const int64_t b = row_ptr[r], h = hstart[r], e = row_ptr[r + 1];
+            unsigned long long w = 0;
+            for (int64_t p = b; p < h; ++p) w += (unsigned long long)head[p].hrem;
+            work[r] = (int64_t)w;
+            acc.add((unsigned long long)(e - h), (unsigned long long)(e - b), w);
+        }
+    }
+    acc.flush(st);
+}
+
+__global__ void k_row_work_warp(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
+                                const tc_head* __restrict__ head, const int64_t* __restrict__ band, int64_t n,
+                                int64_t* __restrict__ work, row_stats* __restrict__ st) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    unsigned long long l_h2 = 0, l_w = 0, l_dh = 0, l_maxh = 0, l_maxd = 0;
-    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+    row_acc acc;
+    for (int64_t r = band[0] + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); r < n; r += warps) {
         const int64_t b = row_ptr[r], h = hstart[r], e = row_ptr[r + 1];
         unsigned long long w = 0;
         for (int64_t p = b + lane; p < h; p += 32) w += (unsigned long long)head[p].hrem;
         for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
         if (lane == 0) {
-            const unsigned long long hv = (unsigned long long)(e - h), d = (unsigned long long)(e - b);
             work[r] = (int64_t)w;
-            l_h2 += hv * hv;
-            l_w += w;
-            l_dh += d * hv;
-            l_maxh = l_maxh > hv ? l_maxh : hv;
-            l_maxd = l_maxd > d ? l_maxd : d;
+            acc.add((unsigned long long)(e - h), (unsigned long long)(e - b), w);
         }
     }
-    if (lane == 0) {
-        atomicAdd(&st->sum_h2, l_h2);
-        atomicAdd(&st->wedges, l_w);
-        atomicAdd(&st->sum_dh, l_dh);
-        atomicMax(&st->max_h, l_maxh);
-        atomicMax(&st->max_d, l_maxd);
-    }
+    acc.flush(st);
 }
 
 int bits_for(int64_t n) {
@@ -219,6 +424,43 @@ tc_status sort_keys(scratch& sc, cub::DoubleBuffer<T>& buf, int64_t count, int e
     uint8_t* tmp = nullptr;
     TC_TRY(sc.get(&tmp, bytes));
     TC_CUDA(cub::DeviceRadixSort::SortKeys(tmp, bytes, buf, count, 0, end_bit, s));
+    return TC_OK;
+}
+
+// Step 4 after the run offsets: row split and cursors, tail placement,
+// then the runs sorted and written by length class.
+template <class C>
+tc_status build_runs(tc_graph* g, cudaStream_t s, int64_t m, int64_t n, int bits, const uint64_t* keys,
+                     uint64_t* slot, const int32_t* dh, const int64_t* hptr, int32_t* big, unsigned int* nbig,
+                     C* hnext, C* tnext, int rows_blocks) {
+    {
+        launch_scope ls("build_hstart", s);
+        k_hstart<<<grid_for(n), kThreads, 0, s>>>(g->row_ptr, dh, hptr, n, g->hstart, hnext, tnext);
+        TC_LAUNCH_CHECK();
+    }
+    {
+        launch_scope ls("build_tail_place", s);
+        k_tail_place<<<grid_for(m), kThreads, 0, s>>>(keys, m, bits, tnext, slot);
+        TC_LAUNCH_CHECK();
+    }
+    {
+        launch_scope ls("build_runs_small", s);
+        k_runs_small<<<rows_blocks, kThreads, 0, s>>>(g->row_ptr, g->hstart, hptr, slot, n, hnext, g->col,
+                                                      g->head, g->edge_tail, big, nbig);
+        TC_LAUNCH_CHECK();
+    }
+    {
+        launch_scope ls("build_runs_mid", s);
+        k_runs_mid<<<sm_count() * 8, 32 * kMidWarps, 0, s>>>(g->row_ptr, g->hstart, hptr, slot, big, nbig, hnext,
+                                                             g->col, g->head, g->edge_tail);
+        TC_LAUNCH_CHECK();
+    }
+    {
+        launch_scope ls("build_runs_big", s);
+        k_runs_big<<<sm_count() * 2, kRunThreads, 0, s>>>(g->row_ptr, g->hstart, hptr, slot, big, nbig, hnext,
+                                                          g->col, g->head, g->edge_tail);
+        TC_LAUNCH_CHECK();
+    }
     return TC_OK;
 }
 
@@ -368,54 +610,48 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
         TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, bytes, degr, g->row_ptr, n + 1, s));
     }
 
-    // ---- 4. rank-space CSR: the m edges sorted once by (lo, hi) give every
-    // N_H(r) in order; the heads N_L(r) need no order
+    // ---- 4. rank-space CSR: every edge placed in its lower end's run of
+    // tails, each run sorted (N_H(r) ascending) and both entries written;
+    // the heads N_L(r) need no order
     if (m > 0) {
-        uint64_t *ka2 = nullptr, *kb2p = nullptr;
-        uint32_t *va = nullptr, *vb = nullptr;
-        int32_t *dh = nullptr, *hcur = nullptr;
+        uint64_t *keys = nullptr, *slot = nullptr;
+        int32_t *dh = nullptr, *big = nullptr;
+        unsigned int* nbig = nullptr;
+        void* hnext = nullptr;   // head cursors (absolute positions)
+        void* tnext = nullptr;   // tail-run cursors (compact order)
         int64_t* hptr = nullptr;
-        TC_TRY(sc.get(&ka2, m));
-        TC_TRY(sc.get(&kb2p, m));
-        TC_TRY(sc.get(&va, m));
-        TC_TRY(sc.get(&vb, m));
+        const bool narrow = e2 < ((int64_t)1 << 32);   // 32-bit cursors suffice
+        TC_TRY(sc.get(&keys, m));
+        TC_TRY(sc.get(&slot, m));
         TC_TRY(sc.get(&dh, n + 1));
-        TC_TRY(sc.get(&hcur, n + 1));
+        TC_TRY(sc.get(&big, n + 1));
+        TC_TRY(sc.get(&nbig, 1));
+        TC_TRY(sc.get((uint8_t**)&hnext, (n + 1) * (narrow ? 4 : 8)));
+        TC_TRY(sc.get((uint8_t**)&tnext, (n + 1) * (narrow ? 4 : 8)));
         TC_TRY(sc.get(&hptr, n + 1));
         TC_CUDA(cudaMemsetAsync(dh, 0, (n + 1) * 4, s));
-        TC_CUDA(cudaMemsetAsync(hcur, 0, (n + 1) * 4, s));
+        TC_CUDA(cudaMemsetAsync(nbig, 0, 4, s));
         {
             launch_scope ls("build_edge_rank_keys", s);
-            k_edge_rank_keys<<<grid_for(m), kThreads, 0, s>>>(g->edge_u, g->edge_v, rank, m, bits, ka2, va, dh);
+            k_edge_rank_keys<<<grid_for(m), kThreads, 0, s>>>(g->edge_u, g->edge_v, rank, m, bits, keys, dh);
             TC_LAUNCH_CHECK();
         }
-        cub::DoubleBuffer<uint64_t> kb2(ka2, kb2p);
-        cub::DoubleBuffer<uint32_t> vb2(va, vb);
-        size_t bytes = 0;
-        TC_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, bytes, kb2, vb2, m, 0, 2 * bits, s));
         size_t sbytes = 0;
         TC_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, sbytes, dh, hptr, n + 1, s));
         uint8_t* tmp = nullptr;
-        TC_TRY(sc.get(&tmp, std::max(bytes, sbytes)));
-        {
-            launch_scope ls("build_sort_edges", s);
-            TC_CUDA(cub::DeviceRadixSort::SortPairs(tmp, bytes, kb2, vb2, m, 0, 2 * bits, s));
-        }
+        TC_TRY(sc.get(&tmp, sbytes));
         {
             launch_scope ls("build_hptr", s);
             TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, sbytes, dh, hptr, n + 1, s));
         }
-        {
-            launch_scope ls("build_hstart", s);
-            k_hstart<<<grid_for(n), kThreads, 0, s>>>(g->row_ptr, dh, n, g->hstart);
-            TC_LAUNCH_CHECK();
-        }
-        {
-            launch_scope ls("build_scatter", s);
-            k_scatter<<<grid_for(m), kThreads, 0, s>>>(kb2.Current(), vb2.Current(), m, bits, g->row_ptr,
-                                                        g->hstart, hptr, hcur, g->col, g->head,
-                                                        g->edge_tail);
-            TC_LAUNCH_CHECK();
+        const int cap = sm_count() * 16;
+        const int rows_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, cap));
+        if (narrow) {
+            TC_TRY(build_runs(g, s, m, n, bits, keys, slot, dh, hptr, big, nbig, (uint32_t*)hnext,
+                              (uint32_t*)tnext, rows_blocks));
+        } else {
+            TC_TRY(build_runs(g, s, m, n, bits, keys, slot, dh, hptr, big, nbig, (unsigned long long*)hnext,
+                              (unsigned long long*)tnext, rows_blocks));
         }
     } else if (n > 0) {
         // no edges: every row is empty
@@ -427,19 +663,29 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
     row_stats* dst_stats = nullptr;
     TC_TRY(sc.get(&dst_stats, 1));
     TC_CUDA(cudaMemsetAsync(dst_stats, 0, sizeof(row_stats), s));
-    if (n > 0) {
-        launch_scope ls("build_row_work", s);
-        int blocks = (int)std::min<int64_t>((n * 32 + kThreads - 1) / kThreads, (int64_t)sm_count() * 16);
-        k_row_work<<<std::max(blocks, 1), kThreads, 0, s>>>(g->row_ptr, g->hstart, g->head, n, g->work,
-                                                            dst_stats);
-        TC_LAUNCH_CHECK();
-    }
     int64_t* d_band = nullptr;
     TC_TRY(sc.get(&d_band, 2));
     {
         launch_scope ls("build_bands", s);
         k_bands<<<1, 1, 0, s>>>(g->row_ptr, n, d_band);
         TC_LAUNCH_CHECK();
+    }
+    if (n > 0) {
+        const int cap = sm_count() * 16;
+        {
+            launch_scope ls("build_row_work_thread", s);
+            const int bt = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)cap);
+            k_row_work_thread<<<std::max(bt, 1), kThreads, 0, s>>>(g->row_ptr, g->hstart, g->head, d_band,
+                                                                   g->work, dst_stats);
+            TC_LAUNCH_CHECK();
+        }
+        {
+            launch_scope ls("build_row_work_warp", s);
+            const int bw = (int)std::min<int64_t>((n * 32 + kThreads - 1) / kThreads, (int64_t)cap);
+            k_row_work_warp<<<std::max(bw, 1), kThreads, 0, s>>>(g->row_ptr, g->hstart, g->head, d_band, n,
+                                                                 g->work, dst_stats);
+            TC_LAUNCH_CHECK();
+        }
     }
     row_stats hst{};
     TC_CUDA(cudaMemcpyAsync(&hst, dst_stats, sizeof(row_stats), cudaMemcpyDeviceToHost, s));
