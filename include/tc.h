@@ -119,6 +119,25 @@ tc_status tc_count(tc_graph* g, uint64_t* d_tri, uint8_t* d_edge_flag,
                    uint64_t* h_tri_total, tc_stream stream);
 
 /*
+ * Per-edge triangle counts t(u, v) = (A² ∘ A)(u, v), the number of
+ * triangles on each edge (section "Notation": T = A² ∘ A, whose row sums
+ * are 2△(v), section "Algebraic Form"), computed by the same pass as
+ * tc_count: wherever tc_count marks an edge as lying in a triangle, this
+ * call adds the number of triangles found there instead.
+ *
+ *   d_tri        [n] uint64, caller labels: △(v).  May be NULL.
+ *   d_edge_tri   [m] uint32, aligned with the canonical edge list of
+ *                tc_graph_info: t(u, v) of that edge.  May be NULL.
+ *   h_tri_total  receives △(G) = Σ t(u, v) / 3.  May be NULL.
+ * Also leaves the counts and edge flags (flag = t > 0) in the graph, so
+ * tc_centrality may follow.  Takes 4 bytes per CSR entry (8 per edge) of
+ * extra device memory, held by the graph until tc_graph_free.  Returns
+ * TC_OK or TC_NO_TRIANGLES.  Synchronises `stream`.
+ */
+tc_status tc_edge_triangles(tc_graph* g, uint64_t* d_tri, uint32_t* d_edge_tri, uint64_t* h_tri_total,
+                            tc_stream stream);
+
+/*
  * Step 3: for every vertex the exact numerator
  *   numer(v) = △(v) + Σ_{u ∈ N(v)} (u ∈ N△(v) ? 1 : 3) · △(u)
  * (the core sum x plus three times the non-core sum y of Algorithm 2), and

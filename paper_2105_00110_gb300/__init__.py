@@ -38,7 +38,7 @@ TC_STRATEGY_BITMAP = 3
 TC_STRATEGY_GLOBAL = 4
 STRATEGIES = {"auto": 0, "bsearch": 1, "merge": 2, "bitmap": 3, "global": 4}
 
-EXPORTED = ["tc_build_csr", "tc_count", "tc_centrality", "tc_divide", "tc_graph_info",
+EXPORTED = ["tc_build_csr", "tc_count", "tc_edge_triangles", "tc_centrality", "tc_divide", "tc_graph_info",
             "tc_copy_edges", "tc_get_stats", "tc_set_strategy", "tc_profile_enable",
             "tc_profile_reset", "tc_profile_read", "tc_launch_count", "tc_graph_free",
             "tc_status_str", "tc_batch_build", "tc_batch_run", "tc_batch_info",
@@ -103,6 +103,8 @@ def lib():
         L.tc_build_csr.argtypes = [vp, vp, i64, i64, u32, vp, ctypes.POINTER(vp)]
         L.tc_count.restype = i32
         L.tc_count.argtypes = [vp, vp, vp, ctypes.POINTER(u64), vp]
+        L.tc_edge_triangles.restype = i32
+        L.tc_edge_triangles.argtypes = [vp, vp, vp, ctypes.POINTER(u64), vp]
         L.tc_centrality.restype = i32
         L.tc_centrality.argtypes = [vp, vp, vp, ctypes.POINTER(u64), vp]
         L.tc_divide.restype = i32
@@ -217,6 +219,15 @@ def tc_count(g, tri=None, edge_flag=None, stream=None):
     total = ctypes.c_uint64()
     st = lib().tc_count(g, _dptr(tri), _dptr(edge_flag), ctypes.byref(total), _stream(stream))
     _check(st, "tc_count")
+    return st, total.value
+
+
+def tc_edge_triangles(g, tri=None, edge_tri=None, stream=None):
+    """(status, △(G)); fills tri [n] uint64 and edge_tri [m] uint32 (t(u, v)
+    per canonical edge) if given."""
+    total = ctypes.c_uint64()
+    st = lib().tc_edge_triangles(g, _dptr(tri), _dptr(edge_tri), ctypes.byref(total), _stream(stream))
+    _check(st, "tc_edge_triangles")
     return st, total.value
 
 
@@ -338,6 +349,12 @@ class Graph:
         flags = torch.empty(self.m, dtype=torch.uint8, device=self.device) if want_flags else None
         st, total = tc_count(self.h, tri, flags, stream)
         return tri, flags, total, st
+
+    def edge_triangles(self, stream=None):
+        tri = torch.empty(self.n, dtype=torch.uint64, device=self.device)
+        et = torch.empty(max(self.m, 1), dtype=torch.int32, device=self.device).view(torch.uint32)
+        st, total = tc_edge_triangles(self.h, tri, et if self.m else None, stream)
+        return tri, et[:self.m], total, st
 
     def centrality(self, stream=None):
         numer = torch.empty(self.n, dtype=torch.uint64, device=self.device)

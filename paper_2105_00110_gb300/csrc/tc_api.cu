@@ -196,6 +196,24 @@ tc_status tc_count(tc_graph* g, uint64_t* d_tri, uint8_t* d_edge_flag, uint64_t*
     return total == 0 ? TC_NO_TRIANGLES : TC_OK;
 }
 
+tc_status tc_edge_triangles(tc_graph* g, uint64_t* d_tri, uint32_t* d_edge_tri, uint64_t* h_tri_total,
+                            tc_stream stream) {
+    if (!g) return TC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->stream = s;
+    g->counted = 0;
+    TC_TRY(run_count(g, s, true));
+    if (d_tri) TC_TRY(export_tri(g, d_tri, s));
+    if (d_edge_tri) TC_TRY(export_edge_counts(g, d_edge_tri, s));
+    unsigned long long total = 0;
+    TC_CUDA(cudaMemcpyAsync(&total, g->counters, 8, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    g->total = total;
+    g->counted = 1;
+    if (h_tri_total) *h_tri_total = total;
+    return total == 0 ? TC_NO_TRIANGLES : TC_OK;
+}
+
 tc_status tc_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, uint64_t* h_den,
                         tc_stream stream) {
     if (!g) return TC_ERR_INVALID_ARG;

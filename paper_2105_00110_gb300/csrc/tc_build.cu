@@ -469,7 +469,7 @@ tc_status build_runs(tc_graph* g, cudaStream_t s, int64_t m, int64_t n, int bits
 void free_graph_memory(tc_graph* g) {
     cudaStream_t s = g->stream;
     void* ptrs[] = {g->edge_u, g->edge_v, g->perm, g->row_ptr, g->col, g->hstart, g->head,
-                    g->edge_tail, g->work, g->tri, g->flag, g->numer, g->counters};
+                    g->edge_tail, g->work, g->tri, g->flag, g->numer, g->counters, g->ecnt};
     for (void* q : ptrs) dfree(q, s);
     free_plan(g->plan, s);
 }

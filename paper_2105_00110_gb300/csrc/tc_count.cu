@@ -31,6 +31,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "tc_internal.cuh"
 
@@ -229,14 +230,38 @@ __device__ __forceinline__ void put_stream(const entry& e, int k, int gpre, stre
     tb.gpre[k] = gpre;
 }
 
+// Marks edge entries that lie in triangles.  Normally `f` holds one flag
+// bit per CSR position; in edge-count mode (EC) it holds one 32-bit
+// counter per CSR position and a mark adds the number of triangles found
+// on that entry, giving t(u, v) = (A² ∘ A)(u, v) on every canonical entry.
+template <bool EC>
+__device__ __forceinline__ void mark(uint32_t* __restrict__ f, int64_t p, uint32_t c) {
+    if (EC) atomicAdd(&f[p], c);
+    else flag_set(f, p);
+}
+// The hits hm (bit k: position pos + k) of one octet (pos 8-aligned).
+template <bool EC>
+__device__ __forceinline__ void mark_octet(uint32_t* __restrict__ f, int64_t pos, uint32_t hm) {
+    if (EC) {
+        while (hm) {
+            const int k = __ffs(hm) - 1;
+            hm &= hm - 1;
+            atomicAdd(&f[pos + k], 1u);
+        }
+    } else if (hm) {
+        // the octet's 8 flag bits lie in one 32-bit word
+        flag_or(f, pos >> 5, hm << (pos & 31));
+    }
+}
+
 // Credits the hits of stream k to △(u) and flags the edge (u, v).
-template <int N>
+template <int N, bool EC>
 __device__ __forceinline__ void close_stream(int k, stream_table<N>& tb, ull* __restrict__ tri,
                                              uint32_t* __restrict__ flag, ull& tv) {
     const uint32_t c = tb.hits[k];
     if (c) {
         atomicAdd(&tri[tb.u[k]], (ull)c);
-        flag_set(flag, tb.va[k] + (tb.fl[k] & 7) - 1);   // twin(u, v): the canonical entry of (u, v)
+        mark<EC>(flag, tb.va[k] + (tb.fl[k] & 7) - 1, c);   // twin(u, v): the canonical entry of (u, v)
         tv += c;
     }
 }
@@ -259,7 +284,7 @@ __device__ __forceinline__ octet load8(const int32_t* __restrict__ col, int64_t 
 // counts the triangle (u, v, w) at the staged index, and the octet's hit
 // flags are set with one 32-bit OR (its 8 flag bits lie in one word, and an
 // OR never clears a flag another thread set).  Returns the hits.
-template <class LK, bool CNT>
+template <class LK, bool CNT, bool EC>
 __device__ __forceinline__ uint32_t visit_octet(const LK& lk, const octet& o, int64_t pos, int off, int len,
                                                 uint32_t* cnt, int64_t h0, ull* __restrict__ tri,
                                                 uint32_t* __restrict__ flag) {
@@ -273,14 +298,13 @@ __device__ __forceinline__ uint32_t visit_octet(const LK& lk, const octet& o, in
                 atomicAdd(&cnt[l], 1u);
             } else {
                 atomicAdd(&tri[o.x[k]], 1ull);
-                flag_set(flag, h0 + l);
+                mark<EC>(flag, h0 + l, 1u);
             }
             bits |= 1u << k;
             ++nh;
         }
     }
-    // the octet's 8 flag bits lie in one 32-bit word (pos is 8-aligned)
-    if (bits) flag_or(flag, pos >> 5, (uint32_t)bits << (pos & 31));
+    mark_octet<EC>(flag, pos, bits);
     return nh;
 }
 
@@ -288,12 +312,10 @@ __device__ __forceinline__ uint32_t visit_octet(const LK& lk, const octet& o, in
 // staged indices of the hits, then the counter atomics — so that the loads
 // of an octet overlap instead of each waiting behind the previous id's
 // atomic.
-template <>
-__device__ __forceinline__ uint32_t visit_octet<lookup_bitmap, true>(const lookup_bitmap& lk, const octet& o,
-                                                                    int64_t pos, int off, int len,
-                                                                    uint32_t* cnt, int64_t h0,
-                                                                    ull* __restrict__ tri,
-                                                                    uint32_t* __restrict__ flag) {
+template <bool EC>
+__device__ __forceinline__ uint32_t visit_octet_bitmap(const lookup_bitmap& lk, const octet& o, int64_t pos,
+                                                       int off, int len, uint32_t* cnt, int64_t h0,
+                                                       ull* __restrict__ tri, uint32_t* __restrict__ flag) {
     uint32_t word[8], boff[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -312,8 +334,7 @@ __device__ __forceinline__ uint32_t visit_octet<lookup_bitmap, true>(const looku
 #pragma unroll
     for (int k = 0; k < 8; ++k)
         if ((hm >> k) & 1u) atomicAdd(&cnt[l[k]], 1u);
-    // the octet's 8 flag bits lie in one 32-bit word (pos is 8-aligned)
-    flag_or(flag, pos >> 5, hm << (pos & 31));
+    mark_octet<EC>(flag, pos, hm);
     return (uint32_t)__popc(hm);
 }
 
@@ -322,7 +343,7 @@ __device__ __forceinline__ uint32_t visit_octet<lookup_bitmap, true>(const looku
 // lane is found from the starts of the next 32 streams that fall inside the
 // current 32-group window (one warp OR-reduction); s_base is the stream
 // holding the group before the window.
-template <class LK, bool CNT, int N, int G>
+template <class LK, bool CNT, int N, int G, bool EC>
 __device__ __forceinline__ void walk_groups(int lane, stream_table<N>& tb, int nc, int gb, int ge,
                                             const LK& lk, uint32_t* cnt, int64_t h0,
                                             const int32_t* __restrict__ col, ull* __restrict__ tri,
@@ -355,7 +376,10 @@ __device__ __forceinline__ void walk_groups(int lane, stream_table<N>& tb, int n
             for (int j = 0; j < G; ++j) o[j] = load8(col, pos + 8 * j);
 #pragma unroll
             for (int j = 0; j < G; ++j)
-                h += visit_octet<LK, CNT>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, h0, tri, flag);
+                if constexpr (std::is_same<LK, lookup_bitmap>::value && CNT)
+                    h += visit_octet_bitmap<EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, h0, tri, flag);
+                else
+                    h += visit_octet<LK, CNT, EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, h0, tri, flag);
         }
         if ((smask & ~1u) == 0) {
             // the whole window lies in one stream
@@ -372,7 +396,7 @@ __device__ __forceinline__ void walk_groups(int lane, stream_table<N>& tb, int n
 // path of A and B into equal diagonals; on ties the A element is consumed
 // first, and a common id is counted when its A element is consumed while
 // the current B element equals it.
-template <int N>
+template <int N, bool EC>
 __device__ __forceinline__ void merge_streams(int lane, int k0, int k1, stream_table<N>& tb,
                                               const int32_t* A, int na, uint32_t* cnt,
                                               const int32_t* __restrict__ col,
@@ -394,7 +418,7 @@ __device__ __forceinline__ void merge_streams(int lane, int k0, int k1, stream_t
             if (ia < na && (jb >= nb || A[ia] <= __ldg(B + jb))) {
                 if (jb < nb && __ldg(B + jb) == A[ia]) {
                     atomicAdd(&cnt[ia], 1u);
-                    flag_set(flag, p0 + jb);
+                    mark<EC>(flag, p0 + jb, 1u);
                     ++found;
                 }
                 ++ia;
@@ -449,7 +473,7 @@ __device__ __forceinline__ int compact_warp(int lane, const entry& e, stream_tab
 constexpr int kWarpG = TC_WARP_G;   // octets (8 ids) per lane per window, warp items
 constexpr int kCtaG = TC_CTA_G;     // octets per lane per window, CTA items
 
-template <bool MERGE>
+template <bool MERGE, bool EC>
 __global__ void __launch_bounds__(TC_CTA_THREADS, 4)
 k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
              const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
@@ -497,18 +521,18 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
                 nxt = fetch_entry(b + 32 + lane, pe, head);   // in flight meanwhile
                 int nc;
                 const int groups = compact_warp<kWarpG>(lane, cur, ws.tb, nc);
-                if (MERGE) merge_streams(lane, 0, nc, ws.tb, ids, hv, cnt, col, flag);
-                else if (use_bitmap) walk_groups<lookup_bitmap, true, 32, kWarpG>(lane, ws.tb, nc, 0, groups, lb, cnt, h0, col, tri, flag);
-                else walk_groups<lookup_sorted, true, 32, kWarpG>(lane, ws.tb, nc, 0, groups, ls, cnt, h0, col, tri, flag);
+                if (MERGE) merge_streams<32, EC>(lane, 0, nc, ws.tb, ids, hv, cnt, col, flag);
+                else if (use_bitmap) walk_groups<lookup_bitmap, true, 32, kWarpG, EC>(lane, ws.tb, nc, 0, groups, lb, cnt, h0, col, tri, flag);
+                else walk_groups<lookup_sorted, true, 32, kWarpG, EC>(lane, ws.tb, nc, 0, groups, ls, cnt, h0, col, tri, flag);
                 __syncwarp();
-                if (lane < nc) close_stream(lane, ws.tb, tri, flag, tv);
+                if (lane < nc) close_stream<32, EC>(lane, ws.tb, tri, flag, tv);
                 __syncwarp();
             }
             for (int i = lane; i < hv; i += 32) {
                 const uint32_t c = cnt[i];
                 if (c) {
                     atomicAdd(&tri[col[h0 + i]], (ull)c);
-                    flag_set(flag, h0 + i);
+                    mark<EC>(flag, h0 + i, c);
                 }
             }
             tv = warp_sum(tv);
@@ -525,7 +549,7 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
 // entries are taken in rounds of 256 (a stream table, the next round's
 // entries loaded while this one streams); the round's units are split
 // evenly over the warps.
-template <int LOOK, bool MERGE>
+template <int LOOK, bool MERGE, bool EC>
 __global__ void __launch_bounds__(TC_CTA_THREADS, TC_CTA_MIN_BLOCKS)
 k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
             const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
@@ -602,18 +626,18 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             if (ng > 0) put_stream(cur, before_c + __popc(nz & ((1u << lane) - 1)), before_g + incl - ng, tb);
             __syncthreads();
             if (MERGE) {
-                merge_streams(lane, (NC * warp) >> 3, (NC * (warp + 1)) >> 3, tb, ls.ids, hv, cnt, col, flag);
+                merge_streams<256, EC>(lane, (NC * warp) >> 3, (NC * (warp + 1)) >> 3, tb, ls.ids, hv, cnt, col, flag);
             } else {
                 const int gb = (int)(((int64_t)GT * warp) >> 3), ge = (int)(((int64_t)GT * (warp + 1)) >> 3);
                 if (LOOK == L_BITMAP)
-                    walk_groups<lookup_bitmap, true, 256, kCtaG>(lane, tb, NC, gb, ge, lb, cnt, h0, col, tri, flag);
+                    walk_groups<lookup_bitmap, true, 256, kCtaG, EC>(lane, tb, NC, gb, ge, lb, cnt, h0, col, tri, flag);
                 else if (LOOK == L_SORTED)
-                    walk_groups<lookup_sorted, true, 256, kCtaG>(lane, tb, NC, gb, ge, ls, cnt, h0, col, tri, flag);
+                    walk_groups<lookup_sorted, true, 256, kCtaG, EC>(lane, tb, NC, gb, ge, ls, cnt, h0, col, tri, flag);
                 else
-                    walk_groups<lookup_global, false, 256, kCtaG>(lane, tb, NC, gb, ge, lg, nullptr, h0, col, tri, flag);
+                    walk_groups<lookup_global, false, 256, kCtaG, EC>(lane, tb, NC, gb, ge, lg, nullptr, h0, col, tri, flag);
             }
             __syncthreads();   // every group of the round is done
-            if (t < NC) close_stream(t, tb, tri, flag, tv);
+            if (t < NC) close_stream<256, EC>(t, tb, tri, flag, tv);
             __syncthreads();   // before the table is overwritten
         }
         tv = warp_sum(tv);
@@ -624,7 +648,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
                 const uint32_t c = cnt[i];
                 if (c) {
                     atomicAdd(&tri[col[h0 + i]], (ull)c);
-                    flag_set(flag, h0 + i);
+                    mark<EC>(flag, h0 + i, c);
                 }
             }
         }
@@ -790,7 +814,7 @@ tc_status shape_for(const void* fn, size_t smem, int& per_sm) {
 
 template <class K>
 tc_status launch_persistent(K kernel, const char* name, size_t smem, int64_t items, cudaStream_t s,
-                            const tc_graph* g, const tc_plan& p, int c, ull* cursor) {
+                            const tc_graph* g, const tc_plan& p, int c, ull* cursor, uint32_t* marks) {
     if (items == 0) return TC_OK;
     int per_sm = 1;
     TC_TRY(shape_for((const void*)kernel, smem, per_sm));
@@ -798,7 +822,7 @@ tc_status launch_persistent(K kernel, const char* name, size_t smem, int64_t ite
     launch_scope ls(name, s);
     kernel<<<(int)blocks, TC_CTA_THREADS, smem, s>>>(g->row_ptr, g->col, g->hstart, g->head,
                                                      p.v[c], p.pb[c], p.pe[c], items, cursor,
-                                                     g->strategy, g->tri, g->flag, g->counters);
+                                                     g->strategy, g->tri, marks, g->counters);
     TC_LAUNCH_CHECK();
     return TC_OK;
 }
@@ -903,41 +927,77 @@ tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s) {
 #undef PLAN_CUDA
 }
 
-tc_status run_count(tc_graph* g, cudaStream_t s) {
+namespace {
+
+// Flag bits from per-entry triangle counts (edge-count mode): each warp
+// turns 32 consecutive counts into one flag word.
+__global__ void k_flags_from_counts(const uint32_t* __restrict__ ecnt, int64_t e2, uint32_t* __restrict__ flag) {
+    const int64_t words = (e2 + 31) >> 5;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < (words << 5); p += stride) {
+        const unsigned bits = __ballot_sync(0xffffffffu, p < e2 && ecnt[p] != 0);
+        if ((threadIdx.x & 31) == 0) flag[p >> 5] = bits;
+    }
+}
+
+template <bool EC>
+tc_status launch_count_kernels(tc_graph* g, cudaStream_t s, uint32_t* marks) {
+    const tc_plan& p = g->plan;
+    ull* cur = g->counters + 1;
+    const bool merge = g->strategy == TC_STRATEGY_MERGE;
+    const char* nm[5] = {EC ? "count_edges_bitmap_l" : "count_bitmap_l", EC ? "count_edges_bitmap_s" : "count_bitmap_s",
+                         EC ? "count_edges_cta_list" : "count_cta_list", EC ? "count_edges_cta_global" : "count_cta_global",
+                         EC ? "count_edges_warp" : "count_warp"};
+    // heaviest classes first; each kernel drains its own item queue
+    TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC>, nm[0], p.smem[TC_CLS_BITMAP_L],
+                             p.count[TC_CLS_BITMAP_L], s, g, p, TC_CLS_BITMAP_L, cur + TC_CLS_BITMAP_L, marks));
+    TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC>, nm[1], p.smem[TC_CLS_BITMAP_S],
+                             p.count[TC_CLS_BITMAP_S], s, g, p, TC_CLS_BITMAP_S, cur + TC_CLS_BITMAP_S, marks));
+    if (p.count[TC_CLS_CTA_LIST] > 0) {
+        // lists longer than the shared budget are searched in place
+        const bool fits = g->strategy != TC_STRATEGY_GLOBAL &&
+                          (int64_t)g->stats.max_out_degree * 8 <= (int64_t)p.smem[TC_CLS_CTA_LIST];
+        if (fits && merge)
+            TC_TRY(launch_persistent(k_count_cta<L_SORTED, true, EC>, nm[2], p.smem[TC_CLS_CTA_LIST],
+                                     p.count[TC_CLS_CTA_LIST], s, g, p, TC_CLS_CTA_LIST, cur + TC_CLS_CTA_LIST,
+                                     marks));
+        else if (fits)
+            TC_TRY(launch_persistent(k_count_cta<L_SORTED, false, EC>, nm[2], p.smem[TC_CLS_CTA_LIST],
+                                     p.count[TC_CLS_CTA_LIST], s, g, p, TC_CLS_CTA_LIST, cur + TC_CLS_CTA_LIST,
+                                     marks));
+        else
+            TC_TRY(launch_persistent(k_count_cta<L_GLOBAL, false, EC>, nm[3], 0, p.count[TC_CLS_CTA_LIST], s, g,
+                                     p, TC_CLS_CTA_LIST, cur + TC_CLS_CTA_LIST, marks));
+    }
+    if (merge)
+        TC_TRY(launch_persistent(k_count_warp<true, EC>, nm[4], 0, p.count[TC_CLS_WARP], s, g, p, TC_CLS_WARP,
+                                 cur + TC_CLS_WARP, marks));
+    else
+        TC_TRY(launch_persistent(k_count_warp<false, EC>, nm[4], 0, p.count[TC_CLS_WARP], s, g, p, TC_CLS_WARP,
+                                 cur + TC_CLS_WARP, marks));
+    return TC_OK;
+}
+
+}  // namespace
+
+tc_status run_count(tc_graph* g, cudaStream_t s, bool edge_counts) {
     const int64_t n = g->n, e2 = 2 * g->m;
     if (g->plan.strategy != g->strategy || g->plan_params_version != g->params_version)
         TC_TRY(make_plan(g, g->strategy, s));
     TC_CUDA(cudaMemsetAsync(g->tri, 0, (n + 1) * 8, s));
     TC_CUDA(cudaMemsetAsync(g->flag, 0, flag_words(e2) * 4, s));
     TC_CUDA(cudaMemsetAsync(g->counters, 0, 8 * 8, s));
-    const tc_plan& p = g->plan;
-    ull* cur = g->counters + 1;
-    const bool merge = g->strategy == TC_STRATEGY_MERGE;
-    // heaviest classes first; each kernel drains its own item queue
-    TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false>, "count_bitmap_l", p.smem[TC_CLS_BITMAP_L],
-                             p.count[TC_CLS_BITMAP_L], s, g, p, TC_CLS_BITMAP_L, cur + TC_CLS_BITMAP_L));
-    TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false>, "count_bitmap_s", p.smem[TC_CLS_BITMAP_S],
-                             p.count[TC_CLS_BITMAP_S], s, g, p, TC_CLS_BITMAP_S, cur + TC_CLS_BITMAP_S));
-    if (p.count[TC_CLS_CTA_LIST] > 0) {
-        // lists longer than the shared budget are searched in place
-        const bool fits = g->strategy != TC_STRATEGY_GLOBAL &&
-                          (int64_t)g->stats.max_out_degree * 8 <= (int64_t)p.smem[TC_CLS_CTA_LIST];
-        if (fits && merge)
-            TC_TRY(launch_persistent(k_count_cta<L_SORTED, true>, "count_cta_list", p.smem[TC_CLS_CTA_LIST],
-                                     p.count[TC_CLS_CTA_LIST], s, g, p, TC_CLS_CTA_LIST, cur + TC_CLS_CTA_LIST));
-        else if (fits)
-            TC_TRY(launch_persistent(k_count_cta<L_SORTED, false>, "count_cta_list", p.smem[TC_CLS_CTA_LIST],
-                                     p.count[TC_CLS_CTA_LIST], s, g, p, TC_CLS_CTA_LIST, cur + TC_CLS_CTA_LIST));
-        else
-            TC_TRY(launch_persistent(k_count_cta<L_GLOBAL, false>, "count_cta_global", 0,
-                                     p.count[TC_CLS_CTA_LIST], s, g, p, TC_CLS_CTA_LIST, cur + TC_CLS_CTA_LIST));
+    if (!edge_counts) return launch_count_kernels<false>(g, s, g->flag);
+    if (!g->ecnt) TC_TRY(dalloc((void**)&g->ecnt, (e2 + 1) * 4, s));
+    TC_CUDA(cudaMemsetAsync(g->ecnt, 0, (e2 + 1) * 4, s));
+    TC_TRY(launch_count_kernels<true>(g, s, g->ecnt));
+    if (e2 > 0) {
+        launch_scope ls("count_edges_flags", s);
+        const int64_t words = (e2 + 31) >> 5;
+        const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((words * 32 + 255) / 256, (int64_t)sm_count() * 16));
+        k_flags_from_counts<<<blocks, 256, 0, s>>>(g->ecnt, e2, g->flag);
+        TC_LAUNCH_CHECK();
     }
-    if (merge)
-        TC_TRY(launch_persistent(k_count_warp<true>, "count_warp", 0, p.count[TC_CLS_WARP], s, g, p,
-                                 TC_CLS_WARP, cur + TC_CLS_WARP));
-    else
-        TC_TRY(launch_persistent(k_count_warp<false>, "count_warp", 0, p.count[TC_CLS_WARP], s, g, p,
-                                 TC_CLS_WARP, cur + TC_CLS_WARP));
     return TC_OK;
 }
 

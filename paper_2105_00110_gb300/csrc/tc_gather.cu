@@ -188,6 +188,13 @@ __global__ void k_export_flags(const uint32_t* __restrict__ flag, const int64_t*
         out[e] = flag_get(flag, edge_tail[e]) ? 1 : 0;
 }
 
+__global__ void k_export_edge_counts(const uint32_t* __restrict__ ecnt, const int64_t* __restrict__ edge_tail,
+                                     int64_t m, uint32_t* __restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = ecnt[edge_tail[e]];
+}
+
 inline int blocks_for(int64_t items, int threads) {
     int64_t b = (items + threads - 1) / threads;
     int64_t cap = (int64_t)sm_count() * 16;
@@ -242,6 +249,15 @@ tc_status export_tri(tc_graph* g, uint64_t* d_tri, cudaStream_t s) {
     if (g->n == 0) return TC_OK;
     launch_scope ls("export_tri", s);
     k_export_tri<<<blocks_for(g->n, 256), 256, 0, s>>>(g->tri, g->perm, g->n, (ull*)d_tri);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+tc_status export_edge_counts(tc_graph* g, uint32_t* d_out, cudaStream_t s) {
+    if (g->m == 0) return TC_OK;
+    if (!g->ecnt) return TC_ERR_STATE;
+    launch_scope ls("export_edge_counts", s);
+    k_export_edge_counts<<<blocks_for(g->m, 256), 256, 0, s>>>(g->ecnt, g->edge_tail, g->m, d_out);
     TC_LAUNCH_CHECK();
     return TC_OK;
 }

@@ -88,6 +88,7 @@ struct tc_graph {
     // workspace of tc_count / tc_centrality
     unsigned long long* tri = nullptr;   // [n], rank space
     uint32_t* flag = nullptr;            // one bit per CSR position (2m bits), set on tail entries
+    uint32_t* ecnt = nullptr;            // [2m] triangles on each tail entry (edge-count mode only)
     unsigned long long* numer = nullptr; // [n], rank space
     unsigned long long* counters = nullptr;  // [8]: 0 total, 1 warp cursor, 2 cta cursor
     int counted = 0;
@@ -145,13 +146,14 @@ void free_graph_memory(tc_graph* g);
 // count (tc_count.cu)
 tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s);
 void free_plan(tc_plan& p, cudaStream_t s);
-tc_status run_count(tc_graph* g, cudaStream_t s);
+tc_status run_count(tc_graph* g, cudaStream_t s, bool edge_counts = false);   // edge_counts: t(u, v) into g->ecnt
 // gather + divide (tc_gather.cu)
 tc_status run_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, cudaStream_t s);
 tc_status run_graph_sums(tc_graph* g, const int32_t* rank_graph, unsigned long long* sums, cudaStream_t s);
 tc_status run_divide(const uint64_t* d_numer, int64_t n, uint64_t den, double* d_tc, cudaStream_t s);
 tc_status export_tri(tc_graph* g, uint64_t* d_tri, cudaStream_t s);
 tc_status export_flags(tc_graph* g, uint8_t* d_flag, cudaStream_t s);
+tc_status export_edge_counts(tc_graph* g, uint32_t* d_out, cudaStream_t s);
 
 }  // namespace tcx
 
