@@ -262,6 +262,36 @@ def run_ours(args, spec, wl_name):
     prof = tcg.tc_profile_read()
     t_ms = ev0.elapsed_time(ev1)
 
+    # ---------------- per-edge triangle counts: the count in edge-count mode
+    # against the plain count, on one built graph (outside the timed step)
+    edge_counts = None
+    if world == 1:
+        g = tcg.Graph(d_src, d_dst, n, stream)
+        et = torch.empty(max(g.m, 1), dtype=torch.int32, device=dev).view(torch.uint32)
+        times = {}
+        for mode in ("count", "edges"):
+            for _ in range(2):
+                if mode == "count":
+                    tcg.tc_count(g.h, tri, None, stream)
+                else:
+                    tcg.tc_edge_triangles(g.h, tri, et[:g.m], stream)
+            torch.cuda.synchronize(dev)
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            for _ in range(3):
+                if mode == "count":
+                    tcg.tc_count(g.h, tri, None, stream)
+                else:
+                    tcg.tc_edge_triangles(g.h, tri, et[:g.m], stream)
+            c1.record(stream)
+            torch.cuda.synchronize(dev)
+            times[mode] = c0.elapsed_time(c1) / 3
+        edge_counts = {"edges_per_s": g.m / (times["edges"] / 1e3), "ms_per_call": times["edges"],
+                       "plain_count_ms_per_call": times["count"],
+                       "sum_over_edges_equals_3_triangles": int(et[:g.m].view(torch.int32).sum().item()) == 3 * total}
+        g.close()
+        del et
+
     # ---------------- end to end from pinned host buffers
     for _ in range(max(1, args.warmup // 2)):
         step(h_src, h_dst, to_host=True)
@@ -327,6 +357,7 @@ def run_ours(args, spec, wl_name):
             "cpu_baseline": cpu,
             "phases_ms_per_step": kernel_ms,
             "count_plus_centrality_edges_per_s": (m / ((count_ms + gather_ms) / 1e3)) if count_ms else None,
+            "edge_triangles": edge_counts,
             "graph_stats": stats,
         }
         print(json.dumps(line))
