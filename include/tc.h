@@ -187,11 +187,12 @@ typedef struct {
     double  sum_out_degree_sq;   /* Σ_v |N_H(v)|²                                       */
     double  wedges;              /* Σ_v C(|N_H(v)|, 2): ids streamed by the count step   */
     double  avg_degeneracy;      /* δ̄ = (1/m) Σ_{(v,u)∈E} min(d(v), d(u))              */
-    int64_t items[4];            /* count-step work items per class: bitmap (small shared
-                                    footprint), bitmap (large), warp list, CTA list     */
-    double  class_bytes[4];      /* algorithmic DRAM bytes of each class's kernel       */
-    double  class_wedges[4];     /* ids streamed by each class                          */
-    double  class_head[4];       /* head entries (lower neighbours) of each class       */
+    int64_t items[5];            /* count-step work items per class: bitmap (small shared
+                                    footprint), bitmap (large), warp, CTA list, thread
+                                    (one thread per tiny vertex)                        */
+    double  class_bytes[5];      /* algorithmic DRAM bytes of each class's kernel       */
+    double  class_wedges[5];     /* ids streamed by each class                          */
+    double  class_head[5];       /* head entries (lower neighbours) of each class       */
     double  count_bytes;         /* algorithmic DRAM bytes of the whole count step      */
     double  centrality_bytes;    /* algorithmic DRAM bytes of the gather + divide step  */
 } tc_graph_stats;

@@ -64,8 +64,8 @@ class GraphStats(ctypes.Structure):
                 ("max_degree", ctypes.c_int64), ("max_out_degree", ctypes.c_int64),
                 ("sum_out_degree_sq", ctypes.c_double), ("wedges", ctypes.c_double),
                 ("avg_degeneracy", ctypes.c_double),
-                ("items", ctypes.c_int64 * 4), ("class_bytes", ctypes.c_double * 4),
-                ("class_wedges", ctypes.c_double * 4), ("class_head", ctypes.c_double * 4),
+                ("items", ctypes.c_int64 * 5), ("class_bytes", ctypes.c_double * 5),
+                ("class_wedges", ctypes.c_double * 5), ("class_head", ctypes.c_double * 5),
                 ("count_bytes", ctypes.c_double), ("centrality_bytes", ctypes.c_double)]
 
     def as_dict(self):
@@ -76,10 +76,10 @@ class GraphStats(ctypes.Structure):
         return d
 
 
-CLASS_NAMES = ["bitmap_s", "bitmap_l", "warp", "cta_list"]
+CLASS_NAMES = ["bitmap_s", "bitmap_l", "warp", "cta_list", "thread"]
 # kernel name (as reported by tc_profile_read) -> item class
 KERNEL_CLASS = {"count_bitmap_s": 0, "count_bitmap_l": 1, "count_warp": 2,
-                "count_cta_list": 3, "count_cta_global": 3}
+                "count_cta_list": 3, "count_cta_global": 3, "count_thread": 4}
 
 
 class KernelTime(ctypes.Structure):

@@ -663,6 +663,67 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
     }
 }
 
+// ------------------------------------------------------------ thread items
+// Tiny middle vertices (|N_H(v)| <= kThreadMaxH, head entries + streamed
+// ids <= kThreadMaxWork) take one thread each: N_H(v) is staged in the
+// thread's own column of shared memory (S[k][t], so that the threads of a
+// warp hit distinct banks), and every stream of the vertex is merged
+// against it.  A hit at staged index a and stream position q is the
+// triangle (u, v, w): △(w) += 1, edges (u, w) at q and (v, w) at h0 + a
+// marked, then per stream △(u) and edge (u, v) at twin, per vertex △(v).
+#ifndef TC_THREAD_MAX_WORK
+#define TC_THREAD_MAX_WORK 64
+#endif
+constexpr int kThreadMaxH = 32;
+constexpr int64_t kThreadMaxWork = TC_THREAD_MAX_WORK;
+
+template <bool EC>
+__global__ void __launch_bounds__(TC_CTA_THREADS)
+k_count_thread(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+               const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
+               const int32_t* __restrict__ it_v, const int64_t* __restrict__ it_pb,
+               const int64_t* __restrict__ it_pe, int64_t n_items, ull* __restrict__ cursor, int strategy,
+               ull* __restrict__ tri, uint32_t* __restrict__ flag, ull* __restrict__ total) {
+    __shared__ int32_t S[kThreadMaxH][TC_CTA_THREADS];
+    const int t = threadIdx.x;
+    ull tv_all = 0;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + t; it < n_items; it += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = it_v[it];
+        const int64_t h0 = hstart[v], h1 = row_ptr[v + 1];
+        const int hv = (int)(h1 - h0);
+        for (int k = 0; k < hv; ++k) S[k][t] = col[h0 + k];
+        ull tv = 0;
+        const int64_t pe = it_pe[it];
+        for (int64_t p = it_pb[it]; p < pe; ++p) {
+            const tc_head rec = head[p];
+            const int64_t q0 = rec.twin + 1;
+            const int len = rec.hrem;
+            uint32_t hits = 0;
+            int a = 0;
+            for (int j = 0; j < len && a < hv; ++j) {
+                const int32_t w = col[q0 + j];
+                while (a < hv && S[a][t] < w) ++a;
+                if (a < hv && S[a][t] == w) {
+                    atomicAdd(&tri[w], 1ull);
+                    mark<EC>(flag, q0 + j, 1u);
+                    mark<EC>(flag, h0 + a, 1u);
+                    ++hits;
+                    ++a;
+                }
+            }
+            if (hits) {
+                atomicAdd(&tri[rec.u], (ull)hits);
+                mark<EC>(flag, rec.twin, hits);
+                tv += hits;
+            }
+        }
+        if (tv) atomicAdd(&tri[v], tv);
+        tv_all += tv;
+    }
+    tv_all = warp_sum(tv_all);
+    if ((t & 31) == 0 && tv_all) atomicAdd(total, tv_all);
+}
+
 // ------------------------------------------------------------ planner
 struct class_acc {
     unsigned long long items[TC_NUM_CLS];
@@ -700,10 +761,12 @@ __global__ void k_classify(const int64_t* __restrict__ row_ptr, const int64_t* _
                 c = warp_bm ? TC_CLS_WARP : cta_s ? TC_CLS_BITMAP_S : cta_l ? TC_CLS_BITMAP_L
                   : warp_list ? TC_CLS_WARP : TC_CLS_CTA_LIST;
             } else {
-                // AUTO: heavy vertices on a CTA bitmap when zeroing it is cheap
-                // next to the work; the rest on a warp (bitmap or list)
+                // AUTO: tiny vertices one per thread; heavy vertices on a CTA
+                // bitmap when zeroing it is cheap next to the work; the rest
+                // on a warp (bitmap or list)
                 const bool heavy = W >= pp.cta_min_work && W >= 2 * words;
-                if (heavy && !warp_bm && cta_s) c = TC_CLS_BITMAP_S;
+                if (hv <= kThreadMaxH && lv + W <= kThreadMaxWork) c = TC_CLS_THREAD;
+                else if (heavy && !warp_bm && cta_s) c = TC_CLS_BITMAP_S;
                 else if (heavy && !warp_bm && cta_l) c = TC_CLS_BITMAP_L;
                 else if (warp_bm || warp_list) c = TC_CLS_WARP;
                 else if (cta_s) c = TC_CLS_BITMAP_S;
@@ -711,7 +774,7 @@ __global__ void k_classify(const int64_t* __restrict__ row_ptr, const int64_t* _
                 else c = TC_CLS_CTA_LIST;
             }
             const int64_t chunk = c == TC_CLS_WARP ? pp.warp_chunk : pp.cta_chunk;
-            chunks = (W + chunk - 1) / chunk;
+            chunks = c == TC_CLS_THREAD ? 1 : (W + chunk - 1) / chunk;
             if (chunks > lv) chunks = lv;
             if (chunks < 1) chunks = 1;
 #pragma unroll
@@ -740,11 +803,15 @@ __global__ void k_classify(const int64_t* __restrict__ row_ptr, const int64_t* _
         }
 }
 
+struct emit_targets {
+    int32_t* v[TC_NUM_CLS];
+    int64_t* pb[TC_NUM_CLS];
+    int64_t* pe[TC_NUM_CLS];
+};
+
 __global__ void k_emit(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
                        int64_t n, const int8_t* __restrict__ cls, const int64_t* __restrict__ cnt,
-                       const int64_t* __restrict__ off, int32_t* v0, int64_t* pb0, int64_t* pe0,
-                       int32_t* v1, int64_t* pb1, int64_t* pe1, int32_t* v2, int64_t* pb2,
-                       int64_t* pe2, int32_t* v3, int64_t* pb3, int64_t* pe3) {
+                       const int64_t* __restrict__ off, emit_targets tg) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int c = cls[i];
@@ -752,9 +819,9 @@ __global__ void k_emit(const int64_t* __restrict__ row_ptr, const int64_t* __res
         const int64_t r = n - 1 - i;
         const int64_t b = row_ptr[r], lv = hstart[r] - b;
         const int64_t k = cnt[c * (n + 1) + i], o = off[c * (n + 1) + i];
-        int32_t* vv = c == 0 ? v0 : c == 1 ? v1 : c == 2 ? v2 : v3;
-        int64_t* pbb = c == 0 ? pb0 : c == 1 ? pb1 : c == 2 ? pb2 : pb3;
-        int64_t* pee = c == 0 ? pe0 : c == 1 ? pe1 : c == 2 ? pe2 : pe3;
+        int32_t* vv = tg.v[c];
+        int64_t* pbb = tg.pb[c];
+        int64_t* pee = tg.pe[c];
         for (int64_t j = 0; j < k; ++j) {
             vv[o + j] = (int32_t)r;
             pbb[o + j] = b + lv * j / k;
@@ -899,15 +966,20 @@ tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s) {
     }
     if (n > 0) {
         launch_scope ls("plan_emit", s);
-        k_emit<<<blocks_for(n), 256, 0, s>>>(g->row_ptr, g->hstart, n, cls, cnt, off, p.v[0], p.pb[0],
-                                             p.pe[0], p.v[1], p.pb[1], p.pe[1], p.v[2], p.pb[2],
-                                             p.pe[2], p.v[3], p.pb[3], p.pe[3]);
+        emit_targets tg;
+        for (int c = 0; c < TC_NUM_CLS; ++c) {
+            tg.v[c] = p.v[c];
+            tg.pb[c] = p.pb[c];
+            tg.pe[c] = p.pe[c];
+        }
+        k_emit<<<blocks_for(n), 256, 0, s>>>(g->row_ptr, g->hstart, n, cls, cnt, off, tg);
         PLAN_CUDA(cudaGetLastError());
     }
     p.smem[TC_CLS_BITMAP_S] = kBitmapSmallSmem;
     p.smem[TC_CLS_BITMAP_L] = kBitmapLargeSmem;
     p.smem[TC_CLS_WARP] = 0;
     p.smem[TC_CLS_CTA_LIST] = kCtaListSmem;
+    p.smem[TC_CLS_THREAD] = 0;
     p.strategy = strategy;
     g->plan_params_version = g->params_version;
     // algorithmic bytes of each class's kernel: stage N_H(v) once (4 hv),
@@ -948,6 +1020,8 @@ tc_status launch_count_kernels(tc_graph* g, cudaStream_t s, uint32_t* marks) {
     const char* nm[5] = {EC ? "count_edges_bitmap_l" : "count_bitmap_l", EC ? "count_edges_bitmap_s" : "count_bitmap_s",
                          EC ? "count_edges_cta_list" : "count_cta_list", EC ? "count_edges_cta_global" : "count_cta_global",
                          EC ? "count_edges_warp" : "count_warp"};
+    TC_TRY(launch_persistent(k_count_thread<EC>, EC ? "count_edges_thread" : "count_thread", 0,
+                             p.count[TC_CLS_THREAD], s, g, p, TC_CLS_THREAD, cur + TC_CLS_THREAD, marks));
     // heaviest classes first; each kernel drains its own item queue
     TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC>, nm[0], p.smem[TC_CLS_BITMAP_L],
                              p.count[TC_CLS_BITMAP_L], s, g, p, TC_CLS_BITMAP_L, cur + TC_CLS_BITMAP_L, marks));

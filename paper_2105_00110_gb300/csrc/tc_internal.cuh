@@ -41,7 +41,8 @@ enum tc_item_class {
     TC_CLS_BITMAP_L = 1,   // CTA, bitmap with a large shared footprint
     TC_CLS_WARP = 2,       // warp, N_H(v) as a sorted list (binary search or merge)
     TC_CLS_CTA_LIST = 3,   // CTA, sorted list in shared memory (or global if it does not fit)
-    TC_NUM_CLS = 4
+    TC_CLS_THREAD = 4,     // one thread per tiny vertex, N_H(v) merged against each stream
+    TC_NUM_CLS = 5
 };
 
 // A head entry (see the layout above).

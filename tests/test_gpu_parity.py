@@ -118,11 +118,11 @@ def test_rmat16_many_tiles(strategy):
     items = res["stats"]["items"]
     assert sum(items) > 0
     if strategy == "auto":
-        assert items[2] > 0                      # warp items (bitmap or list)
+        assert items[2] > 0 and items[4] > 0     # warp items (bitmap or list) and tiny thread items
     if strategy == "bitmap":
         assert items[0] > 0 and items[2] > 0     # CTA bitmaps beyond the per-warp window
     if strategy in ("bsearch", "merge"):
-        assert items[0] == items[1] == 0 and items[2] > 0
+        assert items[0] == items[1] == items[4] == 0 and items[2] > 0
     if strategy == "global":
         assert items[3] == sum(items)
 
