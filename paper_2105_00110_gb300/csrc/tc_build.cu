@@ -590,10 +590,22 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
             k_rank_keys<<<grid_for(n), kThreads, 0, s>>>(deg, n, bits, ra);
             TC_LAUNCH_CHECK();
         }
+        // the sort key is (degree << bits | label): it needs only as many
+        // degree bits as the largest degree has
+        int32_t* d_maxdeg = nullptr;
+        TC_TRY(sc.get(&d_maxdeg, 1));
+        size_t rbytes = 0;
+        TC_CUDA(cub::DeviceReduce::Max(nullptr, rbytes, deg, d_maxdeg, n, s));
+        uint8_t* rtmp = nullptr;
+        TC_TRY(sc.get(&rtmp, rbytes));
+        TC_CUDA(cub::DeviceReduce::Max(rtmp, rbytes, deg, d_maxdeg, n, s));
+        int32_t maxdeg = 0;
+        TC_CUDA(cudaMemcpyAsync(&maxdeg, d_maxdeg, 4, cudaMemcpyDeviceToHost, s));
+        TC_CUDA(cudaStreamSynchronize(s));
         cub::DoubleBuffer<uint64_t> rbuf(ra, rb);
         {
             launch_scope ls("build_sort_rank", s);
-            TC_TRY(sort_keys(sc, rbuf, n, 2 * bits, s));
+            TC_TRY(sort_keys(sc, rbuf, n, bits + bits_for((int64_t)maxdeg + 1), s));
         }
         launch_scope ls("build_rank_apply", s);
         k_rank_apply<<<grid_for(n), kThreads, 0, s>>>(rbuf.Current(), n, bits, g->perm, rank, degr);
