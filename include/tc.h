@@ -119,6 +119,40 @@ tc_status tc_count(tc_graph* g, uint64_t* d_tri, uint8_t* d_edge_flag,
                    uint64_t* h_tri_total, tc_stream stream);
 
 /*
+ * Sharded count (steps 1-2 split across K shards: K GPUs, or K passes on
+ * one).  Every triangle is found exactly once, by one work item of the
+ * count (Procedure 1: at its middle vertex, from its lowest vertex), so the
+ * work items can be dealt out: shard k of K counts the items k, k + K, ...
+ * and returns the partial △(v) of the triangles it found and the flags of
+ * their edges.  Summing the partial △(v) over the shards and OR-ing their
+ * flags gives exactly what tc_count gives; tc_load_counts takes that result
+ * back into a graph so that tc_centrality can follow.  Every shard must
+ * hold the same graph (built from the same pairs).
+ *
+ *   shard, num_shards  0 <= shard < num_shards.
+ *   d_tri        [n] uint64, caller labels: this shard's partial △(v).
+ *   d_edge_flag  [m] uint8, canonical edge order: 1 where this shard found
+ *                a triangle on the edge.
+ *   h_tri_partial receives the triangles this shard found.
+ * Any output may be NULL.  Leaves the graph without valid counts (call
+ * tc_load_counts or tc_count before tc_centrality).  Synchronises `stream`.
+ */
+tc_status tc_count_shard(tc_graph* g, int shard, int num_shards, uint64_t* d_tri, uint8_t* d_edge_flag,
+                         uint64_t* h_tri_partial, tc_stream stream);
+
+/*
+ * Loads complete counts — △(v) [n] uint64 in caller labels and the edge
+ * flags [m] uint8 in canonical edge order, e.g. the sum and the OR of every
+ * shard's tc_count_shard outputs — into g, sets △(G) = Σ △(v) / 3 and makes
+ * g ready for tc_centrality.  Returns TC_ERR_INVALID_ARG if Σ △(v) is not a
+ * multiple of 3 (the inputs cannot be complete counts), TC_NO_TRIANGLES if
+ * △(G) = 0, else TC_OK; h_tri_total (may be NULL) receives △(G).
+ * Synchronises `stream`.
+ */
+tc_status tc_load_counts(tc_graph* g, const uint64_t* d_tri, const uint8_t* d_edge_flag, uint64_t* h_tri_total,
+                         tc_stream stream);
+
+/*
  * Per-edge triangle counts t(u, v) = (A² ∘ A)(u, v), the number of
  * triangles on each edge (section "Notation": T = A² ∘ A, whose row sums
  * are 2△(v), section "Algebraic Form"), computed by the same pass as

@@ -38,7 +38,7 @@ TC_STRATEGY_BITMAP = 3
 TC_STRATEGY_GLOBAL = 4
 STRATEGIES = {"auto": 0, "bsearch": 1, "merge": 2, "bitmap": 3, "global": 4}
 
-EXPORTED = ["tc_build_csr", "tc_count", "tc_edge_triangles", "tc_centrality", "tc_divide", "tc_graph_info",
+EXPORTED = ["tc_build_csr", "tc_count", "tc_count_shard", "tc_load_counts", "tc_edge_triangles", "tc_centrality", "tc_divide", "tc_graph_info",
             "tc_copy_edges", "tc_get_stats", "tc_set_strategy", "tc_profile_enable",
             "tc_profile_reset", "tc_profile_read", "tc_launch_count", "tc_graph_free",
             "tc_status_str", "tc_batch_build", "tc_batch_run", "tc_batch_info",
@@ -103,6 +103,10 @@ def lib():
         L.tc_build_csr.argtypes = [vp, vp, i64, i64, u32, vp, ctypes.POINTER(vp)]
         L.tc_count.restype = i32
         L.tc_count.argtypes = [vp, vp, vp, ctypes.POINTER(u64), vp]
+        L.tc_count_shard.restype = i32
+        L.tc_count_shard.argtypes = [vp, i32, i32, vp, vp, ctypes.POINTER(u64), vp]
+        L.tc_load_counts.restype = i32
+        L.tc_load_counts.argtypes = [vp, vp, vp, ctypes.POINTER(u64), vp]
         L.tc_edge_triangles.restype = i32
         L.tc_edge_triangles.argtypes = [vp, vp, vp, ctypes.POINTER(u64), vp]
         L.tc_centrality.restype = i32
@@ -220,6 +224,35 @@ def tc_count(g, tri=None, edge_flag=None, stream=None):
     st = lib().tc_count(g, _dptr(tri), _dptr(edge_flag), ctypes.byref(total), _stream(stream))
     _check(st, "tc_count")
     return st, total.value
+
+
+def tc_count_shard(g, shard: int, num_shards: int, tri=None, edge_flag=None, stream=None) -> int:
+    """Triangles found by shard `shard` of `num_shards`; fills its partial
+    tri [n] uint64 and edge_flag [m] uint8 if given."""
+    part = ctypes.c_uint64()
+    st = lib().tc_count_shard(g, int(shard), int(num_shards), _dptr(tri), _dptr(edge_flag), ctypes.byref(part),
+                              _stream(stream))
+    _check(st, "tc_count_shard", ok=(TC_OK,))
+    return part.value
+
+
+def tc_load_counts(g, tri, edge_flag, stream=None):
+    """(status, △(G)) after loading complete counts and flags into g."""
+    total = ctypes.c_uint64()
+    st = lib().tc_load_counts(g, _dptr(tri), _dptr(edge_flag) if edge_flag is not None and edge_flag.numel() else None,
+                              ctypes.byref(total), _stream(stream))
+    _check(st, "tc_load_counts")
+    return st, total.value
+
+
+def allreduce_counts(tri, edge_flag, group=None):
+    """The exchange step of a sharded count across processes: sums the
+    partial △(v) and ORs the edge flags (a max over 0/1 bytes) in place,
+    over torch.distributed (NCCL between GPUs, gloo on CPU)."""
+    import torch.distributed as dist
+    dist.all_reduce(tri.view(torch.int64), op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(edge_flag, op=dist.ReduceOp.MAX, group=group)
+    return tri, edge_flag
 
 
 def tc_edge_triangles(g, tri=None, edge_tri=None, stream=None):

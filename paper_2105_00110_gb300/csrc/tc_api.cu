@@ -214,6 +214,41 @@ tc_status tc_edge_triangles(tc_graph* g, uint64_t* d_tri, uint32_t* d_edge_tri, 
     return total == 0 ? TC_NO_TRIANGLES : TC_OK;
 }
 
+tc_status tc_count_shard(tc_graph* g, int shard, int num_shards, uint64_t* d_tri, uint8_t* d_edge_flag,
+                         uint64_t* h_tri_partial, tc_stream stream) {
+    if (!g || num_shards < 1 || shard < 0 || shard >= num_shards) return TC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->stream = s;
+    g->counted = 0;   // partial counts: tc_centrality needs tc_load_counts first
+    TC_TRY(run_count(g, s, false, shard, num_shards));
+    if (d_tri) TC_TRY(export_tri(g, d_tri, s));
+    if (d_edge_flag) TC_TRY(export_flags(g, d_edge_flag, s));
+    unsigned long long part = 0;
+    TC_CUDA(cudaMemcpyAsync(&part, g->counters, 8, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    if (h_tri_partial) *h_tri_partial = part;
+    return TC_OK;
+}
+
+tc_status tc_load_counts(tc_graph* g, const uint64_t* d_tri, const uint8_t* d_edge_flag, uint64_t* h_tri_total,
+                         tc_stream stream) {
+    if (!g || (g->n > 0 && !d_tri) || (g->m > 0 && !d_edge_flag)) return TC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    g->stream = s;
+    g->counted = 0;
+    TC_TRY(import_counts(g, d_tri, d_edge_flag, s));
+    unsigned long long sum = 0;
+    TC_CUDA(cudaMemcpyAsync(&sum, g->counters, 8, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    if (sum % 3 != 0) return TC_ERR_INVALID_ARG;   // Σ △(v) = 3△(G) for any graph
+    g->total = sum / 3;
+    TC_CUDA(cudaMemcpyAsync(g->counters, &g->total, 8, cudaMemcpyHostToDevice, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    g->counted = 1;
+    if (h_tri_total) *h_tri_total = g->total;
+    return g->total == 0 ? TC_NO_TRIANGLES : TC_OK;
+}
+
 tc_status tc_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, uint64_t* h_den,
                         tc_stream stream) {
     if (!g) return TC_ERR_INVALID_ARG;

@@ -479,8 +479,8 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
              const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
              const int32_t* __restrict__ it_v,
              const int64_t* __restrict__ it_pb, const int64_t* __restrict__ it_pe,
-             int64_t n_items, ull* __restrict__ cursor, int strategy, ull* __restrict__ tri,
-             uint32_t* __restrict__ flag, ull* __restrict__ total) {
+             int64_t n_items, int64_t it_off, int64_t it_stride, ull* __restrict__ cursor, int strategy,
+             ull* __restrict__ tri, uint32_t* __restrict__ flag, ull* __restrict__ total) {
     __shared__ __align__(16) warp_smem sm[kCtaWarps];
     const int lane = threadIdx.x & 31;
     warp_smem& ws = sm[threadIdx.x >> 5];
@@ -494,8 +494,9 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
         if (base >= n_items) break;
         const int64_t lim = min(base + kWarpItemsPerFetch, n_items);
         for (int64_t it = base; it < lim; ++it) {
-            const int32_t v = it_v[it];
-            const int64_t pb = it_pb[it], pe = it_pe[it];
+            const int64_t gi = it_off + it_stride * it;   // this shard's it-th item
+            const int32_t v = it_v[gi];
+            const int64_t pb = it_pb[gi], pe = it_pe[gi];
             entry nxt = fetch_entry(pb + lane, pe, head);
             const int64_t h0 = hstart[v], h1 = row_ptr[v + 1];
             const int hv = (int)(h1 - h0);
@@ -555,7 +556,8 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
             const int32_t* __restrict__ it_v,
             const int64_t* __restrict__ it_pb, const int64_t* __restrict__ it_pe,
-            int64_t n_items, ull* __restrict__ cursor, int strategy, ull* __restrict__ tri,
+            int64_t n_items, int64_t it_off, int64_t it_stride, ull* __restrict__ cursor, int strategy,
+            ull* __restrict__ tri,
             uint32_t* __restrict__ flag, ull* __restrict__ total) {
     extern __shared__ __align__(16) uint8_t dyn[];
     __shared__ __align__(16) stream_table<256> tb;
@@ -572,8 +574,9 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         __syncthreads();
         const int64_t it = s_item;
         if (it >= n_items) break;
-        const int32_t v = it_v[it];
-        const int64_t pb = it_pb[it], pe = it_pe[it];
+        const int64_t gi = it_off + it_stride * it;   // this shard's it-th item
+        const int32_t v = it_v[gi];
+        const int64_t pb = it_pb[gi], pe = it_pe[gi];
         entry nxt = fetch_entry(pb + t, pe, head);
         const int64_t h0 = hstart[v], h1 = row_ptr[v + 1];
         const int hv = (int)(h1 - h0);
@@ -682,19 +685,21 @@ __global__ void __launch_bounds__(TC_CTA_THREADS)
 k_count_thread(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
                const int32_t* __restrict__ it_v, const int64_t* __restrict__ it_pb,
-               const int64_t* __restrict__ it_pe, int64_t n_items, ull* __restrict__ cursor, int strategy,
+               const int64_t* __restrict__ it_pe, int64_t n_items, int64_t it_off, int64_t it_stride,
+               ull* __restrict__ cursor, int strategy,
                ull* __restrict__ tri, uint32_t* __restrict__ flag, ull* __restrict__ total) {
     __shared__ int32_t S[kThreadMaxH][TC_CTA_THREADS];
     const int t = threadIdx.x;
     ull tv_all = 0;
     for (int64_t it = blockIdx.x * (int64_t)blockDim.x + t; it < n_items; it += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t v = it_v[it];
+        const int64_t gi = it_off + it_stride * it;   // this shard's it-th item
+        const int32_t v = it_v[gi];
         const int64_t h0 = hstart[v], h1 = row_ptr[v + 1];
         const int hv = (int)(h1 - h0);
         for (int k = 0; k < hv; ++k) S[k][t] = col[h0 + k];
         ull tv = 0;
-        const int64_t pe = it_pe[it];
-        for (int64_t p = it_pb[it]; p < pe; ++p) {
+        const int64_t pe = it_pe[gi];
+        for (int64_t p = it_pb[gi]; p < pe; ++p) {
             const tc_head rec = head[p];
             const int64_t q0 = rec.twin + 1;
             const int len = rec.hrem;
@@ -880,15 +885,20 @@ tc_status shape_for(const void* fn, size_t smem, int& per_sm) {
 }
 
 template <class K>
-tc_status launch_persistent(K kernel, const char* name, size_t smem, int64_t items, cudaStream_t s,
-                            const tc_graph* g, const tc_plan& p, int c, ull* cursor, uint32_t* marks) {
+tc_status launch_persistent(K kernel, const char* name, size_t smem, int64_t all_items, cudaStream_t s,
+                            const tc_graph* g, const tc_plan& p, int c, ull* cursor, uint32_t* marks,
+                            int shard, int num_shards) {
+    // shard k of K takes items k, k + K, k + 2K, ... of the class (heaviest
+    // first, so the shards' work comes out close to equal)
+    const int64_t items = all_items > shard ? (all_items - shard + num_shards - 1) / num_shards : 0;
     if (items == 0) return TC_OK;
     int per_sm = 1;
     TC_TRY(shape_for((const void*)kernel, smem, per_sm));
     int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, items);
     launch_scope ls(name, s);
     kernel<<<(int)blocks, TC_CTA_THREADS, smem, s>>>(g->row_ptr, g->col, g->hstart, g->head,
-                                                     p.v[c], p.pb[c], p.pe[c], items, cursor,
+                                                     p.v[c], p.pb[c], p.pe[c], items, (int64_t)shard,
+                                                     (int64_t)num_shards, cursor,
                                                      g->strategy, g->tri, marks, g->counters);
     TC_LAUNCH_CHECK();
     return TC_OK;
@@ -1013,7 +1023,7 @@ __global__ void k_flags_from_counts(const uint32_t* __restrict__ ecnt, int64_t e
 }
 
 template <bool EC>
-tc_status launch_count_kernels(tc_graph* g, cudaStream_t s, uint32_t* marks) {
+tc_status launch_count_kernels(tc_graph* g, cudaStream_t s, uint32_t* marks, int shard, int num_shards) {
     const tc_plan& p = g->plan;
     ull* cur = g->counters + 1;
     const bool merge = g->strategy == TC_STRATEGY_MERGE;
@@ -1021,12 +1031,12 @@ tc_status launch_count_kernels(tc_graph* g, cudaStream_t s, uint32_t* marks) {
                          EC ? "count_edges_cta_list" : "count_cta_list", EC ? "count_edges_cta_global" : "count_cta_global",
                          EC ? "count_edges_warp" : "count_warp"};
     TC_TRY(launch_persistent(k_count_thread<EC>, EC ? "count_edges_thread" : "count_thread", 0,
-                             p.count[TC_CLS_THREAD], s, g, p, TC_CLS_THREAD, cur + TC_CLS_THREAD, marks));
+                             p.count[TC_CLS_THREAD], s, g, p, TC_CLS_THREAD, cur + TC_CLS_THREAD, marks, shard, num_shards));
     // heaviest classes first; each kernel drains its own item queue
     TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC>, nm[0], p.smem[TC_CLS_BITMAP_L],
-                             p.count[TC_CLS_BITMAP_L], s, g, p, TC_CLS_BITMAP_L, cur + TC_CLS_BITMAP_L, marks));
+                             p.count[TC_CLS_BITMAP_L], s, g, p, TC_CLS_BITMAP_L, cur + TC_CLS_BITMAP_L, marks, shard, num_shards));
     TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC>, nm[1], p.smem[TC_CLS_BITMAP_S],
-                             p.count[TC_CLS_BITMAP_S], s, g, p, TC_CLS_BITMAP_S, cur + TC_CLS_BITMAP_S, marks));
+                             p.count[TC_CLS_BITMAP_S], s, g, p, TC_CLS_BITMAP_S, cur + TC_CLS_BITMAP_S, marks, shard, num_shards));
     if (p.count[TC_CLS_CTA_LIST] > 0) {
         // lists longer than the shared budget are searched in place
         const bool fits = g->strategy != TC_STRATEGY_GLOBAL &&
@@ -1034,37 +1044,37 @@ tc_status launch_count_kernels(tc_graph* g, cudaStream_t s, uint32_t* marks) {
         if (fits && merge)
             TC_TRY(launch_persistent(k_count_cta<L_SORTED, true, EC>, nm[2], p.smem[TC_CLS_CTA_LIST],
                                      p.count[TC_CLS_CTA_LIST], s, g, p, TC_CLS_CTA_LIST, cur + TC_CLS_CTA_LIST,
-                                     marks));
+                                     marks, shard, num_shards));
         else if (fits)
             TC_TRY(launch_persistent(k_count_cta<L_SORTED, false, EC>, nm[2], p.smem[TC_CLS_CTA_LIST],
                                      p.count[TC_CLS_CTA_LIST], s, g, p, TC_CLS_CTA_LIST, cur + TC_CLS_CTA_LIST,
-                                     marks));
+                                     marks, shard, num_shards));
         else
             TC_TRY(launch_persistent(k_count_cta<L_GLOBAL, false, EC>, nm[3], 0, p.count[TC_CLS_CTA_LIST], s, g,
-                                     p, TC_CLS_CTA_LIST, cur + TC_CLS_CTA_LIST, marks));
+                                     p, TC_CLS_CTA_LIST, cur + TC_CLS_CTA_LIST, marks, shard, num_shards));
     }
     if (merge)
         TC_TRY(launch_persistent(k_count_warp<true, EC>, nm[4], 0, p.count[TC_CLS_WARP], s, g, p, TC_CLS_WARP,
-                                 cur + TC_CLS_WARP, marks));
+                                 cur + TC_CLS_WARP, marks, shard, num_shards));
     else
         TC_TRY(launch_persistent(k_count_warp<false, EC>, nm[4], 0, p.count[TC_CLS_WARP], s, g, p, TC_CLS_WARP,
-                                 cur + TC_CLS_WARP, marks));
+                                 cur + TC_CLS_WARP, marks, shard, num_shards));
     return TC_OK;
 }
 
 }  // namespace
 
-tc_status run_count(tc_graph* g, cudaStream_t s, bool edge_counts) {
+tc_status run_count(tc_graph* g, cudaStream_t s, bool edge_counts, int shard, int num_shards) {
     const int64_t n = g->n, e2 = 2 * g->m;
     if (g->plan.strategy != g->strategy || g->plan_params_version != g->params_version)
         TC_TRY(make_plan(g, g->strategy, s));
     TC_CUDA(cudaMemsetAsync(g->tri, 0, (n + 1) * 8, s));
     TC_CUDA(cudaMemsetAsync(g->flag, 0, flag_words(e2) * 4, s));
     TC_CUDA(cudaMemsetAsync(g->counters, 0, 8 * 8, s));
-    if (!edge_counts) return launch_count_kernels<false>(g, s, g->flag);
+    if (!edge_counts) return launch_count_kernels<false>(g, s, g->flag, shard, num_shards);
     if (!g->ecnt) TC_TRY(dalloc((void**)&g->ecnt, (e2 + 1) * 4, s));
     TC_CUDA(cudaMemsetAsync(g->ecnt, 0, (e2 + 1) * 4, s));
-    TC_TRY(launch_count_kernels<true>(g, s, g->ecnt));
+    TC_TRY(launch_count_kernels<true>(g, s, g->ecnt, shard, num_shards));
     if (e2 > 0) {
         launch_scope ls("count_edges_flags", s);
         const int64_t words = (e2 + 31) >> 5;

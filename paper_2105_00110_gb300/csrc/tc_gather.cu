@@ -195,6 +195,29 @@ __global__ void k_export_edge_counts(const uint32_t* __restrict__ ecnt, const in
         out[e] = ecnt[edge_tail[e]];
 }
 
+// Counts and flags handed back in the public layout (caller labels,
+// canonical edge order), e.g. summed / OR-ed over shards: △(v) into rank
+// space with their sum, flags onto the tail entries.
+__global__ void k_import_tri(const uint64_t* __restrict__ in, const int32_t* __restrict__ perm, int64_t n,
+                             ull* __restrict__ tri, ull* __restrict__ sum) {
+    ull local = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+        const ull x = in[perm[r]];
+        tri[r] = x;
+        local += x;
+    }
+    local = warp_sum(local);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(sum, local);
+}
+
+__global__ void k_import_flags(const uint8_t* __restrict__ in, const int64_t* __restrict__ edge_tail, int64_t m,
+                               uint32_t* __restrict__ flag) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        if (in[e]) flag_set(flag, edge_tail[e]);
+}
+
 inline int blocks_for(int64_t items, int threads) {
     int64_t b = (items + threads - 1) / threads;
     int64_t cap = (int64_t)sm_count() * 16;
@@ -259,6 +282,23 @@ tc_status export_edge_counts(tc_graph* g, uint32_t* d_out, cudaStream_t s) {
     launch_scope ls("export_edge_counts", s);
     k_export_edge_counts<<<blocks_for(g->m, 256), 256, 0, s>>>(g->ecnt, g->edge_tail, g->m, d_out);
     TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+tc_status import_counts(tc_graph* g, const uint64_t* d_tri, const uint8_t* d_flag, cudaStream_t s) {
+    const int64_t n = g->n, m = g->m;
+    TC_CUDA(cudaMemsetAsync(g->counters, 0, 8 * 8, s));
+    TC_CUDA(cudaMemsetAsync(g->flag, 0, flag_words(2 * m) * 4, s));
+    if (n > 0) {
+        launch_scope ls("import_tri", s);
+        k_import_tri<<<blocks_for(n, 256), 256, 0, s>>>(d_tri, g->perm, n, g->tri, g->counters);
+        TC_LAUNCH_CHECK();
+    }
+    if (m > 0) {
+        launch_scope ls("import_flags", s);
+        k_import_flags<<<blocks_for(m, 256), 256, 0, s>>>(d_flag, g->edge_tail, m, g->flag);
+        TC_LAUNCH_CHECK();
+    }
     return TC_OK;
 }
 

@@ -147,7 +147,9 @@ void free_graph_memory(tc_graph* g);
 // count (tc_count.cu)
 tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s);
 void free_plan(tc_plan& p, cudaStream_t s);
-tc_status run_count(tc_graph* g, cudaStream_t s, bool edge_counts = false);   // edge_counts: t(u, v) into g->ecnt
+// edge_counts: t(u, v) into g->ecnt; shard k of num_shards counts only the
+// items k, k + num_shards, ... of every class (partial counts and flags)
+tc_status run_count(tc_graph* g, cudaStream_t s, bool edge_counts = false, int shard = 0, int num_shards = 1);
 // gather + divide (tc_gather.cu)
 tc_status run_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, cudaStream_t s);
 tc_status run_graph_sums(tc_graph* g, const int32_t* rank_graph, unsigned long long* sums, cudaStream_t s);
@@ -155,6 +157,8 @@ tc_status run_divide(const uint64_t* d_numer, int64_t n, uint64_t den, double* d
 tc_status export_tri(tc_graph* g, uint64_t* d_tri, cudaStream_t s);
 tc_status export_flags(tc_graph* g, uint8_t* d_flag, cudaStream_t s);
 tc_status export_edge_counts(tc_graph* g, uint32_t* d_out, cudaStream_t s);
+// loads △(v) (caller labels) and canonical edge flags; counters[0] = Σ △(v)
+tc_status import_counts(tc_graph* g, const uint64_t* d_tri, const uint8_t* d_flag, cudaStream_t s);
 
 }  // namespace tcx
 

@@ -49,3 +49,66 @@ def test_two_rank_aggregation():
 
 def test_single_rank_identity():
     assert bench.aggregate(3.0, 4.0, 5, 6, 1) == (3.0, 4.0, 5, 6)
+
+
+def _triangles(src, dst, n):
+    """All triangles a < b < c of the simple graph on the pairs (small n)."""
+    A = np.zeros((n, n), dtype=bool)
+    for a, b in zip(src.tolist(), dst.tolist()):
+        if a != b:
+            A[a, b] = A[b, a] = True
+    out = []
+    for a in range(n):
+        for b in np.nonzero(A[a, a + 1:])[0] + a + 1:
+            for c in np.nonzero(A[b, b + 1:] & A[a, b + 1:])[0] + b + 1:
+                out.append((a, int(b), int(c)))
+    return out
+
+
+def _exchange_worker(rank, world, port, q):
+    import torch
+
+    import graphgen as gg
+    import oracle
+    import paper_2105_00110_gb300 as tcg
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    s, d, n = gg.gnp(40, 0.25, 61)
+    ref = oracle.run(s, d, n)
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(ref["ptr"]))
+    keep = ref["adj"] > rows
+    eu, ev = rows[keep], ref["adj"][keep]
+    index = {(int(a), int(b)): i for i, (a, b) in enumerate(zip(eu, ev))}
+    tri = np.zeros(n, np.uint64)
+    flags = np.zeros(len(eu), np.uint8)
+    for i, (a, b, c) in enumerate(_triangles(s, d, n)):
+        if i % world != rank:            # this rank's share of the triangles
+            continue
+        for x in (a, b, c):
+            tri[x] += 1
+        for e in ((a, b), (a, c), (b, c)):
+            flags[index[e]] = 1
+    t = torch.from_numpy(tri.view(np.int64)).view(torch.uint64)
+    f = torch.from_numpy(flags)
+    tcg.allreduce_counts(t, f)
+    ok = (np.array_equal(t.view(torch.int64).numpy().view(np.uint64), ref["tri"]) and
+          np.array_equal(f.numpy(), ref["flag"][keep]))
+    q.put((rank, ok, int(ref["total"])))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_count_exchange():
+    # the exchange step of a sharded count: partial counts sum, flags OR
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_exchange_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=180) for _ in procs]
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert all(ok for _, ok, _ in out)
+    assert out[0][2] > 10                # the graph has triangles to split
