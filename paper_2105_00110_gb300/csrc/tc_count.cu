@@ -19,14 +19,21 @@
 //
 // Counts are aggregated on chip before the 64-bit integer atomics: per
 // staged id (shared counters flushed once per item), per lower neighbour
-// (one counter per batch segment), per middle vertex (a register).
+// (one counter per stream), per middle vertex (a register).
 //
-// Streaming: a warp takes 32 lower neighbours at a time (a batch), keeps the
-// non-empty streams as compacted segments and walks their concatenation
-// with lane-consecutive ids (coalesced loads).  The segment of each lane is
-// found from a 32-bit mask of the segment starts inside the current
-// 32-id window (one warp OR-reduction), and every lane keeps 4 windows in
-// flight.
+// Streaming: a batch of head entries (32 for a warp item, 256 per round for
+// a CTA item) becomes a compacted table of streams, read in 8-aligned
+// octets of ids — one 32-byte load, a whole sector, per octet — with ids
+// outside the stream masked; each lane takes G consecutive octets per
+// window and finds its stream from a 32-bit mask of the stream starts in
+// the window (one warp OR-reduction).
+//
+// Item classes (planner below): CTA bitmaps of two shared sizes, warp
+// items (bitmap or sorted list), CTA sorted lists (shared or global), and
+// one thread per tiny vertex.  Two switches ride along every kernel: the
+// edge-count mode (EC), which adds per-entry triangle counts where the
+// normal mode sets flag bits, and an item offset/stride, which restricts a
+// launch to one shard's share of the items.
 #include <cub/cub.cuh>
 
 #include <algorithm>
