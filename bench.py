@@ -480,9 +480,12 @@ def run_batched(args, spec, wl_name):
     t_max, e2e_max, edges_all, e2e_all = aggregate(t_ms, e2e_ms, edges, e2e_edges, world, dev)
     if rank == 0:
         peak, peak_kind = peaks()
-        top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+        # the dominant kernel among those with an algorithmic byte model (the
+        # count classes); the build's run kernels, which can take longer on
+        # many tiny graphs, are scatter-bound and carry none
         bytes_per = {name: stats["class_bytes"][c] for name, c in tcg.KERNEL_CLASS.items()}
-        bytes_per["gather_warp"] = None
+        modelled = {k: v for k, v in prof.items() if bytes_per.get(k)}
+        top = max(modelled.items(), key=lambda kv: kv[1][1]) if modelled else None
         roof = None
         if top and bytes_per.get(top[0]):
             name, (nl, tot) = top

@@ -237,6 +237,17 @@ tc_status tc_get_stats(const tc_graph* g, tc_graph_stats* out);
 tc_status tc_set_strategy(tc_graph* g, int strategy);
 
 /*
+ * Planner settings of the count step (no counterpart in the paper; they
+ * change speed, never results): params3[0] = work W(v) at or above which a
+ * vertex may become CTA items, params3[1] = target wedges per CTA item (a
+ * heavy vertex is split into chunks of about this size; each chunk stages
+ * N_H(v) again), params3[2] = the same for warp items.  The next tc_count
+ * re-plans.  Defaults 4096, 4194304, 16384.
+ */
+tc_status tc_set_plan_params(tc_graph* g, const int64_t* params3);
+tc_status tc_get_plan_params(const tc_graph* g, int64_t* out3);
+
+/*
  * Optional device timing of every library kernel: when enabled, each
  * launch is bracketed by CUDA events on its own stream, and
  * tc_profile_read returns, per kernel name, the launch count and the

@@ -39,7 +39,7 @@ TC_STRATEGY_GLOBAL = 4
 STRATEGIES = {"auto": 0, "bsearch": 1, "merge": 2, "bitmap": 3, "global": 4}
 
 EXPORTED = ["tc_build_csr", "tc_count", "tc_count_shard", "tc_load_counts", "tc_edge_triangles", "tc_centrality", "tc_divide", "tc_graph_info",
-            "tc_copy_edges", "tc_get_stats", "tc_set_strategy", "tc_profile_enable",
+            "tc_copy_edges", "tc_get_stats", "tc_set_strategy", "tc_set_plan_params", "tc_get_plan_params", "tc_profile_enable",
             "tc_profile_reset", "tc_profile_read", "tc_launch_count", "tc_graph_free",
             "tc_status_str", "tc_batch_build", "tc_batch_run", "tc_batch_info",
             "tc_batch_copy_edges", "tc_batch_get_stats", "tc_batch_autotune", "tc_batch_get_params",
@@ -120,6 +120,10 @@ def lib():
         L.tc_copy_edges.argtypes = [vp, vp, vp, vp]
         L.tc_get_stats.restype = i32
         L.tc_get_stats.argtypes = [vp, ctypes.POINTER(GraphStats)]
+        L.tc_set_plan_params.restype = i32
+        L.tc_set_plan_params.argtypes = [vp, vp]
+        L.tc_get_plan_params.restype = i32
+        L.tc_get_plan_params.argtypes = [vp, vp]
         L.tc_set_strategy.restype = i32
         L.tc_set_strategy.argtypes = [vp, i32]
         L.tc_profile_enable.restype = i32
@@ -318,6 +322,17 @@ def tc_set_strategy(g, strategy):
     if isinstance(strategy, str):
         strategy = STRATEGIES[strategy]
     _check(lib().tc_set_strategy(g, int(strategy)), "tc_set_strategy", ok=(TC_OK,))
+
+
+def tc_set_plan_params(g, cta_min_work: int, cta_chunk: int, warp_chunk: int):
+    arr = (ctypes.c_int64 * 3)(int(cta_min_work), int(cta_chunk), int(warp_chunk))
+    _check(lib().tc_set_plan_params(g, arr), "tc_set_plan_params", ok=(TC_OK,))
+
+
+def tc_get_plan_params(g):
+    arr = (ctypes.c_int64 * 3)()
+    _check(lib().tc_get_plan_params(g, arr), "tc_get_plan_params", ok=(TC_OK,))
+    return dict(cta_min_work=arr[0], cta_chunk=arr[1], warp_chunk=arr[2])
 
 
 def tc_profile_enable(on: bool = True):

@@ -289,6 +289,23 @@ tc_status tc_get_stats(const tc_graph* g, tc_graph_stats* out) {
     return TC_OK;
 }
 
+tc_status tc_set_plan_params(tc_graph* g, const int64_t* params3) {
+    if (!g || !params3 || params3[0] < 0 || params3[1] < 1 || params3[2] < 1) return TC_ERR_INVALID_ARG;
+    g->params.cta_min_work = params3[0];
+    g->params.cta_chunk = params3[1];
+    g->params.warp_chunk = params3[2];
+    g->params_version += 1;   // the next count re-plans
+    return TC_OK;
+}
+
+tc_status tc_get_plan_params(const tc_graph* g, int64_t* out3) {
+    if (!g || !out3) return TC_ERR_INVALID_ARG;
+    out3[0] = g->params.cta_min_work;
+    out3[1] = g->params.cta_chunk;
+    out3[2] = g->params.warp_chunk;
+    return TC_OK;
+}
+
 tc_status tc_set_strategy(tc_graph* g, int strategy) {
     if (!g || strategy < TC_STRATEGY_AUTO || strategy > TC_STRATEGY_GLOBAL) return TC_ERR_INVALID_ARG;
     g->strategy = strategy;
