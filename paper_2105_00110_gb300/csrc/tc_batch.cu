@@ -305,7 +305,7 @@ tc_status tc_batch_autotune(tc_batch* b, int reps, tc_stream stream) {
     // candidate planner settings: when a vertex is heavy enough for a CTA
     // item, and how much work one CTA or warp item carries
     const tc_plan_params cands[] = {
-        {4096, 4194304, 16384}, {4096, 65536, 16384}, {1024, 65536, 16384}, {16384, 65536, 16384},
+        {4096, 4194304, 32768}, {4096, 65536, 16384}, {1024, 65536, 16384}, {16384, 65536, 16384},
         {4096, 32768, 8192},    {4096, 131072, 32768}, {1024, 32768, 4096},  {4096, 65536, 65536},
     };
     cudaEvent_t e0, e1;

@@ -56,7 +56,7 @@ struct __align__(16) tc_head {
 struct tc_plan_params {
     int64_t cta_min_work = 4096;   // W(v) at or above which v may become CTA items
     int64_t cta_chunk = 4194304;   // target wedges per CTA item (each chunk re-stages N_H(v))
-    int64_t warp_chunk = 16384;    // target wedges per warp item
+    int64_t warp_chunk = 32768;    // target wedges per warp item
 };
 
 struct tc_plan {
