@@ -647,8 +647,10 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
                     walk_groups<lookup_global, false, 256, kCtaG, EC>(lane, tb, NC, gb, ge, lg, nullptr, h0, col, tri, flag);
             }
             __syncthreads();   // every group of the round is done
+            // no barrier after the closes: the next round rewrites the table
+            // only after its first barrier, which every thread reaches once
+            // its own close is done
             if (t < NC) close_stream<256, EC>(t, tb, tri, flag, tv);
-            __syncthreads();   // before the table is overwritten
         }
         tv = warp_sum(tv);
         if (lane == 0) s_tv[warp] = tv;
