@@ -222,3 +222,28 @@ def test_repeatable_and_relabel_invariant():
     c = gpu_run(ps, pd, n)
     np.testing.assert_array_equal(c["tri"][perm], a["tri"])
     np.testing.assert_array_equal(c["numer"][perm], a["numer"])
+
+
+def test_planner_settings_change_no_result():
+    # chunk sizes and the CTA threshold move work between kernels and items;
+    # counts, flags and TC stay the same
+    s, d, n = gg.rmat(15, seed=0x5EED0300)
+    g = tcg.Graph(torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), n)
+    try:
+        assert tcg.tc_get_plan_params(g.h) == dict(cta_min_work=4096, cta_chunk=4194304, warp_chunk=32768)
+        runs = []
+        for params in ((4096, 4194304, 32768), (256, 1024, 512), (1 << 40, 1 << 40, 1 << 40), (0, 1, 1)):
+            tcg.tc_set_plan_params(g.h, *params)
+            tri, flags, total, _ = g.count()
+            _, tcv, _, _ = g.centrality()
+            torch.cuda.synchronize()
+            runs.append((total, tri.view(torch.int64).cpu(), flags.cpu(), tcv.view(torch.int64).cpu(),
+                         g.stats()["items"]))
+        for r in runs[1:]:
+            assert r[0] == runs[0][0]
+            assert torch.equal(r[1], runs[0][1]) and torch.equal(r[2], runs[0][2]) and torch.equal(r[3], runs[0][3])
+        assert runs[1][4] != runs[0][4]          # the plan did change
+        with pytest.raises(tcg.TCError):
+            tcg.tc_set_plan_params(g.h, 4096, 0, 1)
+    finally:
+        g.close()
