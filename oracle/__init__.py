@@ -72,6 +72,8 @@ def _load():
             lib.og_numer_algebraic.argtypes = [vp, vp, vp, vp]
             lib.og_sample.restype = ctypes.c_int
             lib.og_sample.argtypes = [vp, vp, i64, vp, vp, vp]
+            lib.og_sample_tri.restype = ctypes.c_int
+            lib.og_sample_tri.argtypes = [vp, vp, i64, vp, vp]
             lib.og_div_rn.restype = ctypes.c_double
             lib.og_div_rn.argtypes = [u64, u64]
             lib.og_div_rn_long.restype = ctypes.c_double
@@ -140,6 +142,18 @@ class OracleGraph:
         if with_rows:
             return tri, num, rows[: int((self.ptr[vs + 1] - self.ptr[vs]).sum())]
         return tri, num
+
+    def sample_tri(self, vertices):
+        """△(v) and the rows t(v, u), u ∈ N(v) ascending, at the given vertices
+        (rows concatenated in sample order): (tri, row_t)."""
+        vs = np.ascontiguousarray(vertices, dtype=np.int64)
+        tri = np.zeros(len(vs), dtype=np.uint64)
+        deg = self.ptr[vs + 1] - self.ptr[vs]
+        rows = np.zeros(max(int(deg.sum()), 1), dtype=np.uint64)
+        rc = _load().og_sample_tri(self._h, _p(vs), len(vs), _p(tri), _p(rows))
+        if rc != 0:
+            raise RuntimeError("og_sample_tri failed (%d)" % rc)
+        return tri, rows[: int(deg.sum())]
 
     def run(self, mode: str = "definition") -> dict:
         """Everything the path computes, in the caller's vertex labels.

@@ -37,6 +37,9 @@
  *                       with the marker-array membership test of Procedure 1
  *                       (mark N(v), scan N(u)); used for sampled checks on
  *                       graphs too large for the full routines.
+ *   og_sample_tri       △(v) and the row of T = A² ∘ A at chosen vertices
+ *                       only (marker test), for graphs whose hubs make the
+ *                       sampled numerator too costly.
  *   og_div_rn           TC(v) = numer(v) / (3△(G)) rounded to nearest-even
  *                       binary64 (one exact rational, one rounding).
  *
@@ -335,6 +338,36 @@ int og_sample(const og_graph* g, const int64_t* vs, int64_t k,
     }
     free(mark);
     free(cache);
+    return 0;
+}
+
+/* The cheap half of og_sample, for graphs whose hubs make the numerator
+ * too costly to sample: tri_out[i] = △(vs[i]) by the marker test, and
+ * row_t (rows of the sampled vertices concatenated in sample order)
+ * t(v,u) = |N(v) ∩ N(u)| for every u in N(v) (section "Notation": the
+ * entries of T = A² ∘ A in row v).  Cost per vertex: Σ_{u∈N(v)} d(u).
+ * Returns 0, -1 on a bad vertex id, -2 on allocation failure. */
+int og_sample_tri(const og_graph* g, const int64_t* vs, int64_t k, uint64_t* tri_out, uint64_t* row_t) {
+    int64_t n = g->n;
+    uint8_t* mark = (uint8_t*)calloc((size_t)n + 1, 1);
+    if (!mark) return -2;
+    int64_t out = 0;
+    for (int64_t s = 0; s < k; ++s) {
+        int64_t v = vs[s];
+        if (v < 0 || v >= n) { free(mark); return -1; }
+        for (int64_t p = g->ptr[v]; p < g->ptr[v + 1]; ++p) mark[g->adj[p]] = 1;
+        uint64_t twice = 0;
+        for (int64_t p = g->ptr[v]; p < g->ptr[v + 1]; ++p) {
+            int32_t u = g->adj[p];
+            uint64_t common = 0;
+            for (int64_t q = g->ptr[u]; q < g->ptr[u + 1]; ++q) common += mark[g->adj[q]];
+            if (row_t) row_t[out++] = common;
+            twice += common;
+        }
+        for (int64_t p = g->ptr[v]; p < g->ptr[v + 1]; ++p) mark[g->adj[p]] = 0;
+        tri_out[s] = twice / 2;
+    }
+    free(mark);
     return 0;
 }
 

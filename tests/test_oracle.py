@@ -239,6 +239,22 @@ def test_sample_matches_full(rmat10):
     assert np.array_equal(rows, want)
 
 
+def test_sample_tri_matches_full_and_brute(rmat10):
+    # the cheap sampler (△ and rows of T only) against the full routines and,
+    # on a tiny graph, against the O(n^3) brute force
+    s, d, n, r = rmat10
+    g = oracle.OracleGraph(s, d, n)
+    vs = np.array([0, 5, 17, 1000, n - 1] + list(np.argsort(-np.diff(r["ptr"]))[:5]), np.int64)
+    tri, rows = g.sample_tri(vs)
+    assert np.array_equal(tri, r["tri"][vs])
+    want = np.concatenate([r["t"][r["ptr"][v]:r["ptr"][v + 1]] for v in vs])
+    assert np.array_equal(rows, want)
+    s2, d2, n2 = gg.gnp(30, 0.3, 77)
+    b = brute(s2, d2, n2)
+    tri2, _ = oracle.OracleGraph(s2, d2, n2).sample_tri(np.arange(n2))
+    assert [int(x) for x in tri2] == list(b["tri"])
+
+
 def test_plausible_mistakes_are_caught():
     """Mistakes a restatement could make, applied to the oracle's outputs on
     the fixtures, are each rejected by a pin."""
