@@ -135,3 +135,36 @@ def test_batch_rejects_out_of_graph_ids():
         tcg.Batch(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(),
                   np.array([0, 2, 4]), np.array([3, 3]))
     assert ei.value.status == tcg.TC_ERR_INVALID_ARG
+
+
+def test_full_batched_workload_sampled():
+    # the bench's batched workload at full size (8192 graphs): per-graph
+    # totals add up, and sampled members equal the oracle and the single path
+    graphs = gg.batch_config3(8192, 0x5EED0003)
+    src, dst, off, nv = tcg.pack_graphs(graphs)
+    b = tcg.Batch(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(), off, nv)
+    out = b.run()
+    torch.cuda.synchronize()
+    tri = out["tri"].view(torch.int64)
+    totals = out["totals"].view(torch.int64).cpu().numpy()
+    voff = torch.from_numpy(np.asarray(b.voff, np.int64)).cuda()
+    per = torch.zeros(len(graphs), dtype=torch.int64, device="cuda")
+    owner = torch.searchsorted(voff[1:], torch.arange(int(voff[-1]), device="cuda"), right=True)
+    per.index_add_(0, owner, tri)
+    np.testing.assert_array_equal(per.cpu().numpy(), 3 * totals)
+    rnd = random.Random(9)
+    pick = rnd.sample(range(len(graphs)), 24)
+    tri_h = tri.cpu().numpy()
+    tc_h = out["tc"].view(torch.int64).cpu().numpy()
+    for k in pick:
+        s, d, n = graphs[k]
+        v0, v1 = b.voff[k], b.voff[k + 1]
+        if n <= 3000:
+            ref = oracle.run(s, d, n)
+            np.testing.assert_array_equal(tri_h[v0:v1], ref["tri"].astype(np.int64))
+            np.testing.assert_array_equal(tc_h[v0:v1], ref["tc"].view(np.int64))
+        one = tcg.triangle_centrality(torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), n)
+        np.testing.assert_array_equal(tri_h[v0:v1], one["tri"].view(torch.int64).cpu().numpy())
+        np.testing.assert_array_equal(tc_h[v0:v1], one["tc"].view(torch.int64).cpu().numpy())
+        assert int(totals[k]) == one["total"]
+    b.close()
