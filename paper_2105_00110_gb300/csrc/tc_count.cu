@@ -50,13 +50,22 @@ typedef unsigned long long ull;
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kCtaWarps = TC_CTA_THREADS / 32;
+// threads of the CTA-item kernel (one head entry per thread per round)
+#ifndef TC_CTA_ITEM_THREADS
+#define TC_CTA_ITEM_THREADS 256
+#endif
+constexpr int kCtaT = TC_CTA_ITEM_THREADS;
+constexpr int kCtaItemWarps = kCtaT / 32;
 #ifndef TC_CTA_MIN_BLOCKS
-#define TC_CTA_MIN_BLOCKS 4   // CTAs per SM the CTA-item kernels are compiled for
+#define TC_CTA_MIN_BLOCKS (1024 / TC_CTA_ITEM_THREADS)   // CTAs per SM the CTA-item kernels are compiled for
 #endif
 
 // Planner constants.
 // 40 KB keeps four CTAs per SM (the register limit) with room left for L1
-constexpr int64_t kBitmapSmallSmem = 40 * 1024;   // dynamic smem of the small-bitmap CTA kernel
+#ifndef TC_BM_S_KB
+#define TC_BM_S_KB 40
+#endif
+constexpr int64_t kBitmapSmallSmem = TC_BM_S_KB * 1024;   // dynamic smem of the small-bitmap CTA kernel
 constexpr int64_t kBitmapLargeSmem = 100 * 1024;  // ... of the large-bitmap CTA kernel
 constexpr int64_t kCtaListSmem = 100 * 1024;      // ... of the CTA sorted-list kernel
 
@@ -558,7 +567,7 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
 // entries loaded while this one streams); the round's units are split
 // evenly over the warps.
 template <int LOOK, bool MERGE, bool EC>
-__global__ void __launch_bounds__(TC_CTA_THREADS, TC_CTA_MIN_BLOCKS)
+__global__ void __launch_bounds__(kCtaT, TC_CTA_MIN_BLOCKS)
 k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
             const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
             const int32_t* __restrict__ it_v,
@@ -567,13 +576,13 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             ull* __restrict__ tri,
             uint32_t* __restrict__ flag, ull* __restrict__ total) {
     extern __shared__ __align__(16) uint8_t dyn[];
-    __shared__ __align__(16) stream_table<256> tb;
+    __shared__ __align__(16) stream_table<kCtaT> tb;
     __shared__ int64_t s_item;
-    __shared__ ull s_tv[kCtaWarps];
-    __shared__ uint32_t s_scan[kCtaWarps];
-    __shared__ int s_cnt[kCtaWarps];
+    __shared__ ull s_tv[kCtaItemWarps];
+    __shared__ uint32_t s_scan[kCtaItemWarps];
+    __shared__ int s_cnt[kCtaItemWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int t = threadIdx.x, nt = TC_CTA_THREADS;
+    const int t = threadIdx.x, nt = kCtaT;
     auto cbar = [] { __syncthreads(); };
     for (;;) {
         __syncthreads();
@@ -592,7 +601,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         lookup_sorted ls{};
         lookup_global lg{};
         if (LOOK == L_BITMAP) {
-            lb = build_bitmap(t, nt, dyn, v, h0, hv, col[h1 - 1] - v, col, cnt, cbar, s_scan, lane, warp, kCtaWarps);
+            lb = build_bitmap(t, nt, dyn, v, h0, hv, col[h1 - 1] - v, col, cnt, cbar, s_scan, lane, warp, kCtaItemWarps);
         } else if (LOOK == L_SORTED) {
             int32_t* ids = (int32_t*)dyn;
             cnt = (uint32_t*)(ids + hv);
@@ -606,9 +615,9 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             lg = lookup_global{col + h0, hv};
         }
         ull tv = 0;
-        for (int64_t r0 = pb; r0 < pe; r0 += 256) {
+        for (int64_t r0 = pb; r0 < pe; r0 += kCtaT) {
             const entry cur = nxt;
-            nxt = fetch_entry(r0 + 256 + t, pe, head);   // in flight meanwhile
+            nxt = fetch_entry(r0 + kCtaT + t, pe, head);   // in flight meanwhile
             // compact the round's non-empty streams: warp scans of the group
             // counts, then the warp totals
             const int ng = entry_groups<kCtaG>(cur);
@@ -626,7 +635,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             __syncthreads();
             int before_g = 0, before_c = 0, GT = 0, NC = 0;
 #pragma unroll
-            for (int k = 0; k < kCtaWarps; ++k) {
+            for (int k = 0; k < kCtaItemWarps; ++k) {
                 const int sg = (int)s_scan[k], sc = s_cnt[k];
                 before_g += k < warp ? sg : 0;
                 before_c += k < warp ? sc : 0;
@@ -636,21 +645,21 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             if (ng > 0) put_stream(cur, before_c + __popc(nz & ((1u << lane) - 1)), before_g + incl - ng, tb);
             __syncthreads();
             if (MERGE) {
-                merge_streams<256, EC>(lane, (NC * warp) >> 3, (NC * (warp + 1)) >> 3, tb, ls.ids, hv, cnt, col, flag);
+                merge_streams<kCtaT, EC>(lane, (NC * warp) / kCtaItemWarps, (NC * (warp + 1)) / kCtaItemWarps, tb, ls.ids, hv, cnt, col, flag);
             } else {
-                const int gb = (int)(((int64_t)GT * warp) >> 3), ge = (int)(((int64_t)GT * (warp + 1)) >> 3);
+                const int gb = (int)(((int64_t)GT * warp) / kCtaItemWarps), ge = (int)(((int64_t)GT * (warp + 1)) / kCtaItemWarps);
                 if (LOOK == L_BITMAP)
-                    walk_groups<lookup_bitmap, true, 256, kCtaG, EC>(lane, tb, NC, gb, ge, lb, cnt, h0, col, tri, flag);
+                    walk_groups<lookup_bitmap, true, kCtaT, kCtaG, EC>(lane, tb, NC, gb, ge, lb, cnt, h0, col, tri, flag);
                 else if (LOOK == L_SORTED)
-                    walk_groups<lookup_sorted, true, 256, kCtaG, EC>(lane, tb, NC, gb, ge, ls, cnt, h0, col, tri, flag);
+                    walk_groups<lookup_sorted, true, kCtaT, kCtaG, EC>(lane, tb, NC, gb, ge, ls, cnt, h0, col, tri, flag);
                 else
-                    walk_groups<lookup_global, false, 256, kCtaG, EC>(lane, tb, NC, gb, ge, lg, nullptr, h0, col, tri, flag);
+                    walk_groups<lookup_global, false, kCtaT, kCtaG, EC>(lane, tb, NC, gb, ge, lg, nullptr, h0, col, tri, flag);
             }
             __syncthreads();   // every group of the round is done
             // no barrier after the closes: the next round rewrites the table
             // only after its first barrier, which every thread reaches once
             // its own close is done
-            if (t < NC) close_stream<256, EC>(t, tb, tri, flag, tv);
+            if (t < NC) close_stream<kCtaT, EC>(t, tb, tri, flag, tv);
         }
         tv = warp_sum(tv);
         if (lane == 0) s_tv[warp] = tv;
@@ -666,7 +675,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         }
         if (t == 0) {
             ull sum = 0;
-            for (int k = 0; k < kCtaWarps; ++k) sum += s_tv[k];
+            for (int k = 0; k < kCtaItemWarps; ++k) sum += s_tv[k];
             if (sum) {
                 atomicAdd(&tri[v], sum);
                 atomicAdd(total, sum);
@@ -870,7 +879,7 @@ int g_nshapes = 0;
 smem_attr g_attrs[16];
 int g_nattrs = 0;
 
-tc_status shape_for(const void* fn, size_t smem, int& per_sm) {
+tc_status shape_for(const void* fn, size_t smem, int threads, int& per_sm) {
     std::lock_guard<std::mutex> lk(g_shape_mu);
     for (int i = 0; i < g_nshapes; ++i)
         if (g_shapes[i].fn == fn && g_shapes[i].smem == smem) {
@@ -887,7 +896,7 @@ tc_status shape_for(const void* fn, size_t smem, int& per_sm) {
             else if (a < g_nattrs) g_attrs[a].max_smem = smem;
         }
     }
-    TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TC_CTA_THREADS, smem));
+    TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
     per_sm = std::max(per_sm, 1);
     if (g_nshapes < 32) g_shapes[g_nshapes++] = launch_shape{fn, smem, per_sm};
     return TC_OK;
@@ -896,16 +905,16 @@ tc_status shape_for(const void* fn, size_t smem, int& per_sm) {
 template <class K>
 tc_status launch_persistent(K kernel, const char* name, size_t smem, int64_t all_items, cudaStream_t s,
                             const tc_graph* g, const tc_plan& p, int c, ull* cursor, uint32_t* marks,
-                            int shard, int num_shards) {
+                            int shard, int num_shards, int threads = TC_CTA_THREADS) {
     // shard k of K takes items k, k + K, k + 2K, ... of the class (heaviest
     // first, so the shards' work comes out close to equal)
     const int64_t items = all_items > shard ? (all_items - shard + num_shards - 1) / num_shards : 0;
     if (items == 0) return TC_OK;
     int per_sm = 1;
-    TC_TRY(shape_for((const void*)kernel, smem, per_sm));
+    TC_TRY(shape_for((const void*)kernel, smem, threads, per_sm));
     int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, items);
     launch_scope ls(name, s);
-    kernel<<<(int)blocks, TC_CTA_THREADS, smem, s>>>(g->row_ptr, g->col, g->hstart, g->head,
+    kernel<<<(int)blocks, threads, smem, s>>>(g->row_ptr, g->col, g->hstart, g->head,
                                                      p.v[c], p.pb[c], p.pe[c], items, (int64_t)shard,
                                                      (int64_t)num_shards, cursor,
                                                      g->strategy, g->tri, marks, g->counters);
@@ -1040,12 +1049,15 @@ tc_status launch_count_kernels(tc_graph* g, cudaStream_t s, uint32_t* marks, int
                          EC ? "count_edges_cta_list" : "count_cta_list", EC ? "count_edges_cta_global" : "count_cta_global",
                          EC ? "count_edges_warp" : "count_warp"};
     TC_TRY(launch_persistent(k_count_thread<EC>, EC ? "count_edges_thread" : "count_thread", 0,
-                             p.count[TC_CLS_THREAD], s, g, p, TC_CLS_THREAD, cur + TC_CLS_THREAD, marks, shard, num_shards));
+                             p.count[TC_CLS_THREAD], s, g, p, TC_CLS_THREAD, cur + TC_CLS_THREAD, marks, shard,
+                             num_shards));
     // heaviest classes first; each kernel drains its own item queue
     TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC>, nm[0], p.smem[TC_CLS_BITMAP_L],
-                             p.count[TC_CLS_BITMAP_L], s, g, p, TC_CLS_BITMAP_L, cur + TC_CLS_BITMAP_L, marks, shard, num_shards));
+                             p.count[TC_CLS_BITMAP_L], s, g, p, TC_CLS_BITMAP_L, cur + TC_CLS_BITMAP_L, marks,
+                             shard, num_shards, kCtaT));
     TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC>, nm[1], p.smem[TC_CLS_BITMAP_S],
-                             p.count[TC_CLS_BITMAP_S], s, g, p, TC_CLS_BITMAP_S, cur + TC_CLS_BITMAP_S, marks, shard, num_shards));
+                             p.count[TC_CLS_BITMAP_S], s, g, p, TC_CLS_BITMAP_S, cur + TC_CLS_BITMAP_S, marks,
+                             shard, num_shards, kCtaT));
     if (p.count[TC_CLS_CTA_LIST] > 0) {
         // lists longer than the shared budget are searched in place
         const bool fits = g->strategy != TC_STRATEGY_GLOBAL &&
@@ -1053,14 +1065,14 @@ tc_status launch_count_kernels(tc_graph* g, cudaStream_t s, uint32_t* marks, int
         if (fits && merge)
             TC_TRY(launch_persistent(k_count_cta<L_SORTED, true, EC>, nm[2], p.smem[TC_CLS_CTA_LIST],
                                      p.count[TC_CLS_CTA_LIST], s, g, p, TC_CLS_CTA_LIST, cur + TC_CLS_CTA_LIST,
-                                     marks, shard, num_shards));
+                                     marks, shard, num_shards, kCtaT));
         else if (fits)
             TC_TRY(launch_persistent(k_count_cta<L_SORTED, false, EC>, nm[2], p.smem[TC_CLS_CTA_LIST],
                                      p.count[TC_CLS_CTA_LIST], s, g, p, TC_CLS_CTA_LIST, cur + TC_CLS_CTA_LIST,
-                                     marks, shard, num_shards));
+                                     marks, shard, num_shards, kCtaT));
         else
             TC_TRY(launch_persistent(k_count_cta<L_GLOBAL, false, EC>, nm[3], 0, p.count[TC_CLS_CTA_LIST], s, g,
-                                     p, TC_CLS_CTA_LIST, cur + TC_CLS_CTA_LIST, marks, shard, num_shards));
+                                     p, TC_CLS_CTA_LIST, cur + TC_CLS_CTA_LIST, marks, shard, num_shards, kCtaT));
     }
     if (merge)
         TC_TRY(launch_persistent(k_count_warp<true, EC>, nm[4], 0, p.count[TC_CLS_WARP], s, g, p, TC_CLS_WARP,
