@@ -298,6 +298,8 @@ def run_ours(args, spec, wl_name):
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    tcg.tc_profile_reset()
+    tcg.tc_profile_enable(True)
     e0.record(stream)
     e2e_edges = 0
     for _ in range(args.steps):
@@ -305,6 +307,8 @@ def run_ours(args, spec, wl_name):
         e2e_edges += m2
     e1.record(stream)
     barrier()
+    tcg.tc_profile_enable(False)
+    e2e_prof = tcg.tc_profile_read()
     e2e_ms = e0.elapsed_time(e1)
     # the raw upload of the step's pairs on this machine (explains e2e - value)
     h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -361,7 +365,10 @@ def run_ours(args, spec, wl_name):
                     "h2d_bytes_per_step": 2 * np_pairs * 4,
                     "d2h_bytes_per_step": n * 8 * 2 + 8,
                     "ms_per_step": e2e_max / args.steps,
-                    "h2d_gb_per_s_measured": round(h2d_gbs, 1)},
+                    "h2d_gb_per_s_measured": round(h2d_gbs, 1),
+                    "kernel_ms_per_step": round(sum(v[1] for v in e2e_prof.values()) / args.steps, 2),
+                    "top_kernels_ms_per_step": {k: round(v[1] / args.steps, 2) for k, v in
+                                                sorted(e2e_prof.items(), key=lambda kv: -kv[1][1])[:6]}},
             "gpu_launches": int(launches),
             "roofline": roof,
             "cpu_baseline": cpu,

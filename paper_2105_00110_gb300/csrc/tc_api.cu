@@ -2,9 +2,11 @@
 #include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "tc_internal.cuh"
@@ -110,6 +112,46 @@ void dfree(void* p, cudaStream_t s) {
 }
 
 void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+int64_t library_kernels(const char* site, int64_t size, int64_t bits,
+                        const std::function<cudaError_t(cudaStream_t)>& call) {
+    static std::mutex mu;
+    static std::map<std::tuple<std::string, int64_t, int64_t>, int64_t> known;
+    const auto key = std::make_tuple(std::string(site), size, bits);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = known.find(key);
+        if (it != known.end()) return it->second;
+    }
+    int64_t kernels = 1;   // if the count cannot be taken, the call counts once
+    cudaStream_t probe = nullptr;
+    if (cudaStreamCreateWithFlags(&probe, cudaStreamNonBlocking) == cudaSuccess) {
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(probe, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const cudaError_t e = call(probe);
+            if (cudaStreamEndCapture(probe, &graph) == cudaSuccess && e == cudaSuccess && graph) {
+                size_t nn = 0;
+                if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0) {
+                    std::vector<cudaGraphNode_t> nodes(nn);
+                    if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess) {
+                        int64_t k = 0;
+                        for (size_t i = 0; i < nn; ++i) {
+                            cudaGraphNodeType t;
+                            if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+                        }
+                        kernels = k;
+                    }
+                }
+            }
+            if (graph) cudaGraphDestroy(graph);
+        }
+        cudaGetLastError();   // a failed capture leaves no error behind for the caller
+        cudaStreamDestroy(probe);
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    known[key] = kernels;
+    return kernels;
+}
 
 void note_launch(const char* name, cudaStream_t s, int phase) {
     if (phase == 0) {

@@ -423,7 +423,13 @@ tc_status sort_keys(scratch& sc, cub::DoubleBuffer<T>& buf, int64_t count, int e
     TC_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, bytes, buf, count, 0, end_bit, s));
     uint8_t* tmp = nullptr;
     TC_TRY(sc.get(&tmp, bytes));
+    // called inside a launch_scope: the sort's own kernels counted beyond it
+    const int64_t k = library_kernels("radix_sort_keys", count, end_bit, [&](cudaStream_t p) {
+        cub::DoubleBuffer<T> probe = buf;   // the real call flips buf's selector
+        return cub::DeviceRadixSort::SortKeys(tmp, bytes, probe, count, 0, end_bit, p);
+    });
     TC_CUDA(cub::DeviceRadixSort::SortKeys(tmp, bytes, buf, count, 0, end_bit, s));
+    add_launches(k - 1);
     return TC_OK;
 }
 
@@ -531,7 +537,9 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
         TC_TRY(sc.get(&tmp, bytes));
         {
             launch_scope ls("build_unique", s);
-            TC_CUDA(cub::DeviceSelect::Unique(tmp, bytes, sorted, uniq, d_nsel, np, s));
+            TC_TRY(run_library("select_unique", np, 0, true, s, [&](cudaStream_t st) {
+                return cub::DeviceSelect::Unique(tmp, bytes, sorted, uniq, d_nsel, np, st);
+            }));
         }
         int64_t h_sel = 0;
         uint64_t last = 0;
@@ -598,7 +606,12 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
         TC_CUDA(cub::DeviceReduce::Max(nullptr, rbytes, deg, d_maxdeg, n, s));
         uint8_t* rtmp = nullptr;
         TC_TRY(sc.get(&rtmp, rbytes));
-        TC_CUDA(cub::DeviceReduce::Max(rtmp, rbytes, deg, d_maxdeg, n, s));
+        {
+            launch_scope ls("build_max_degree", s);
+            TC_TRY(run_library("reduce_max", n, 0, true, s, [&](cudaStream_t st) {
+                return cub::DeviceReduce::Max(rtmp, rbytes, deg, d_maxdeg, n, st);
+            }));
+        }
         int32_t maxdeg = 0;
         TC_CUDA(cudaMemcpyAsync(&maxdeg, d_maxdeg, 4, cudaMemcpyDeviceToHost, s));
         TC_CUDA(cudaStreamSynchronize(s));
@@ -619,7 +632,9 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
         uint8_t* tmp = nullptr;
         TC_TRY(sc.get(&tmp, bytes));
         launch_scope ls("build_row_ptr", s);
-        TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, bytes, degr, g->row_ptr, n + 1, s));
+        TC_TRY(run_library("scan_i64", n + 1, 0, true, s, [&](cudaStream_t st) {
+            return cub::DeviceScan::ExclusiveSum(tmp, bytes, degr, g->row_ptr, n + 1, st);
+        }));
     }
 
     // ---- 4. rank-space CSR: every edge placed in its lower end's run of
@@ -654,7 +669,9 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
         TC_TRY(sc.get(&tmp, sbytes));
         {
             launch_scope ls("build_hptr", s);
-            TC_CUDA(cub::DeviceScan::ExclusiveSum(tmp, sbytes, dh, hptr, n + 1, s));
+            TC_TRY(run_library("scan_i32", n + 1, 0, true, s, [&](cudaStream_t st) {
+                return cub::DeviceScan::ExclusiveSum(tmp, sbytes, dh, hptr, n + 1, st);
+            }));
         }
         const int cap = sm_count() * 16;
         const int rows_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, cap));

@@ -456,7 +456,10 @@ struct warp_smem {
     uint8_t region[kWarpSmem];
     stream_table<32> tb;
 };
-constexpr int kWarpItemsPerFetch = 2;
+#ifndef TC_WARP_FETCH
+#define TC_WARP_FETCH 2
+#endif
+constexpr int kWarpItemsPerFetch = TC_WARP_FETCH;
 
 __device__ __forceinline__ bool warp_bitmap_fits(int64_t words, int64_t hv) {
     return hv < 65536 && bitmap_bytes(words, hv) <= kWarpSmem;
@@ -980,8 +983,10 @@ tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s) {
     {
         launch_scope ls("plan_scan", s);
         for (int c = 0; c < TC_NUM_CLS; ++c)
-            PLAN_CUDA(cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, cnt + c * (n + 1), off + c * (n + 1),
-                                                    n + 1, s));
+            PLAN_TRY(run_library("scan_plan", n + 1, 0, c == 0, s, [&](cudaStream_t st) {
+                return cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, cnt + c * (n + 1), off + c * (n + 1),
+                                                     n + 1, st);
+            }));
     }
     class_acc h{};
     PLAN_CUDA(cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));

@@ -30,6 +30,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+
 #include "tc.h"
 
 #define TC_WARP_CAP 512          // N_H(v) ids staged per warp item
@@ -130,6 +132,22 @@ void dfree(void* p, cudaStream_t s);
 
 // Launch accounting and optional per-kernel event timing.
 void add_launches(int64_t k);   // counts launches made without note_launch
+// Kernels one call of a library routine (CUB) launches, for the launch
+// count: the call is captured once per (site, size, bits) into a graph on a
+// private stream — capturing records the launches without running them —
+// and the graph's kernel nodes are counted.
+int64_t library_kernels(const char* site, int64_t size, int64_t bits,
+                        const std::function<cudaError_t(cudaStream_t)>& call);
+// Runs a library call on s and adds its kernels to the launch count (less
+// one when a launch_scope around it already counted the site).
+template <class F>
+tc_status run_library(const char* site, int64_t size, int64_t bits, bool in_scope, cudaStream_t s, F call) {
+    const int64_t k = library_kernels(site, size, bits, std::function<cudaError_t(cudaStream_t)>(call));
+    const cudaError_t e = call(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    add_launches(in_scope ? k - 1 : k);
+    return TC_OK;
+}
 void note_launch(const char* name, cudaStream_t s, int phase);  // phase 0 before, 1 after
 struct launch_scope {
     const char* name; cudaStream_t s;
