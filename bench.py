@@ -321,14 +321,11 @@ def run_ours(args, spec, wl_name):
     tcg.tc_profile_enable(False)
     e2e_prof = tcg.tc_profile_read()
     e2e_ms = e0.elapsed_time(e1)
-    # the raw upload of the step's pairs on this machine (explains e2e - value)
-    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    h0.record(stream)
-    d_src.copy_(h_src, non_blocking=True)
-    d_dst.copy_(h_dst, non_blocking=True)
-    h1.record(stream)
-    torch.cuda.synchronize(dev)
-    h2d_gbs = 2 * np_pairs * 4 / (h0.elapsed_time(h1) / 1e3) / 1e9
+    # the pair upload inside each end-to-end build, timed by the library
+    # (explains e2e - value); kernels are the other entries
+    up = e2e_prof.pop("copy_h2d_pairs", (0, 0.0))
+    upload_ms = up[1] / args.steps if up[0] else None
+    h2d_gbs = (2 * np_pairs * 4 / (upload_ms / 1e3) / 1e9) if upload_ms else None
 
     t_max, e2e_max, edges_all, e2e_edges_all = aggregate(t_ms, e2e_ms, edges, e2e_edges, world, dev)
 
@@ -387,7 +384,8 @@ def run_ours(args, spec, wl_name):
                     "h2d_bytes_per_step": 2 * np_pairs * 4,
                     "d2h_bytes_per_step": n * 8 * 2 + 8,
                     "ms_per_step": e2e_max / args.steps,
-                    "h2d_gb_per_s_measured": round(h2d_gbs, 1),
+                    "upload_ms_per_step": round(upload_ms, 2) if upload_ms else None,
+                    "h2d_gb_per_s_measured": round(h2d_gbs, 1) if h2d_gbs else None,
                     "kernel_ms_per_step": round(sum(v[1] for v in e2e_prof.values()) / args.steps, 2),
                     "host_ms_per_step_by_call": {k: round(v / (args.steps + max(1, args.warmup // 2)), 2)
                                                  for k, v in host_ms.items()},

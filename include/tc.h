@@ -251,8 +251,10 @@ tc_status tc_get_plan_params(const tc_graph* g, int64_t* out3);
  * Optional device timing of every library kernel: when enabled, each
  * launch is bracketed by CUDA events on its own stream, and
  * tc_profile_read returns, per kernel name, the launch count and the
- * summed event time since the last reset.  Timing adds two event records
- * per launch; leave it off for throughput runs.
+ * summed event time since the last reset.  The upload of host pairs in
+ * tc_build_csr is timed too, as the entry "copy_h2d_pairs" (not a kernel:
+ * tc_launch_count does not count it).  Timing adds two event records per
+ * launch; leave it off for throughput runs.
  */
 tc_status tc_profile_enable(int on);
 tc_status tc_profile_reset(void);

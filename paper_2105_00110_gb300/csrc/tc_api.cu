@@ -153,9 +153,9 @@ int64_t library_kernels(const char* site, int64_t size, int64_t bits,
     return kernels;
 }
 
-void note_launch(const char* name, cudaStream_t s, int phase) {
+void note_launch(const char* name, cudaStream_t s, int phase, bool counts) {
     if (phase == 0) {
-        g_launches.fetch_add(1, std::memory_order_relaxed);
+        if (counts) g_launches.fetch_add(1, std::memory_order_relaxed);
         std::lock_guard<std::mutex> lk(g_prof_mu);
         if (g_prof_on) {
             t_start = take_event();

@@ -497,6 +497,7 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
         void *a = nullptr, *b = nullptr;
         TC_TRY(sc.get((uint8_t**)&a, np * id_bytes));
         TC_TRY(sc.get((uint8_t**)&b, np * id_bytes));
+        copy_scope cs("copy_h2d_pairs", s);
         TC_CUDA(cudaMemcpyAsync(a, src, np * id_bytes, cudaMemcpyHostToDevice, s));
         TC_CUDA(cudaMemcpyAsync(b, dst, np * id_bytes, cudaMemcpyHostToDevice, s));
         dsrc = a;

@@ -148,11 +148,19 @@ tc_status run_library(const char* site, int64_t size, int64_t bits, bool in_scop
     add_launches(in_scope ? k - 1 : k);
     return TC_OK;
 }
-void note_launch(const char* name, cudaStream_t s, int phase);  // phase 0 before, 1 after
+// phase 0 before, 1 after; counts = false times a copy without counting a launch
+void note_launch(const char* name, cudaStream_t s, int phase, bool counts = true);
 struct launch_scope {
     const char* name; cudaStream_t s;
     launch_scope(const char* n, cudaStream_t st) : name(n), s(st) { note_launch(name, s, 0); }
     ~launch_scope() { note_launch(name, s, 1); }
+};
+// Times the copies issued inside it under `name` (profile entries named
+// "copy_*"); they are not kernel launches.
+struct copy_scope {
+    const char* name; cudaStream_t s;
+    copy_scope(const char* n, cudaStream_t st) : name(n), s(st) { note_launch(name, s, 0, false); }
+    ~copy_scope() { note_launch(name, s, 1, false); }
 };
 
 int sm_count();

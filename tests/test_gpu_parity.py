@@ -247,3 +247,27 @@ def test_planner_settings_change_no_result():
             tcg.tc_set_plan_params(g.h, 4096, 0, 1)
     finally:
         g.close()
+
+
+def test_upload_timed_not_counted():
+    # host pairs: the profile times their upload as "copy_h2d_pairs"; the
+    # launch count is the same as for the same pairs already on the device
+    s, d, n = gg.rmat(12, seed=0x5EED0400)
+    hs, hd = torch.from_numpy(s).pin_memory(), torch.from_numpy(d).pin_memory()
+    counts, profs = [], []
+    for src, dst in ((hs, hd), (hs.cuda(), hd.cuda())):
+        torch.cuda.synchronize()
+        tcg.tc_profile_reset()
+        tcg.tc_profile_enable(True)
+        l0 = tcg.tc_launch_count()
+        g = tcg.tc_build_csr(src, dst, n)
+        torch.cuda.synchronize()
+        counts.append(tcg.tc_launch_count() - l0)
+        tcg.tc_profile_enable(False)
+        profs.append(tcg.tc_profile_read())
+        tcg.tc_graph_free(g)
+    assert counts[0] == counts[1] > 0
+    launches, ms = profs[0]["copy_h2d_pairs"]
+    assert launches == 1 and ms > 0
+    assert "copy_h2d_pairs" not in profs[1]
+    assert {k: v[0] for k, v in profs[0].items() if k != "copy_h2d_pairs"} == {k: v[0] for k, v in profs[1].items()}
