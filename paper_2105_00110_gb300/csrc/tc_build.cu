@@ -140,20 +140,28 @@ __global__ void k_tail_place(const uint64_t* __restrict__ keys, int64_t m, int b
 // canonical id -> t, and the head entry in row hi (N_L(hi) in any order) at
 // the next free slot of its cursor, as the record
 // {r, |{w ∈ N_H(r) : w > hi}| = e - t - 1, twin = t}.
-template <class C>
-__device__ __forceinline__ void emit_tail(int64_t r, int64_t t, int64_t e, uint64_t x, C* __restrict__ hnext,
-                                          int32_t* __restrict__ col, tc_head* __restrict__ head,
-                                          int64_t* __restrict__ edge_tail) {
-    const int32_t hi = (int32_t)(x >> 32);
-    col[t] = hi;
+__device__ __forceinline__ void write_tail(int64_t r, int64_t t, int64_t e, uint64_t x, int64_t hp,
+                                           int32_t* __restrict__ col, tc_head* __restrict__ head,
+                                           int64_t* __restrict__ edge_tail) {
+    col[t] = (int32_t)(x >> 32);
     edge_tail[x & 0xffffffffull] = t;
-    const int64_t hp = (int64_t)atomicAdd(&hnext[hi], (C)1);
     tc_head rec;
     rec.u = (int32_t)r;
     rec.hrem = (int32_t)(e - t - 1);
     rec.twin = t;
     head[hp] = rec;   // one 16-byte store
 }
+
+template <class C>
+__device__ __forceinline__ void emit_tail(int64_t r, int64_t t, int64_t e, uint64_t x, C* __restrict__ hnext,
+                                          int32_t* __restrict__ col, tc_head* __restrict__ head,
+                                          int64_t* __restrict__ edge_tail) {
+    const int64_t hp = (int64_t)atomicAdd(&hnext[(int32_t)(x >> 32)], (C)1);
+    write_tail(r, t, e, x, hp, col, head, edge_tail);
+}
+
+// Short runs handled together by one warp in k_runs_small.
+constexpr int kSmallGroup = 8;
 
 // Every run is sorted by bitonic merges in the form whose compare-exchanges
 // all put the smaller key at the lower index: the first step of the k-merge
@@ -184,10 +192,16 @@ __device__ __forceinline__ void run_network_step(uint64_t* key, int len, int P, 
     }
 }
 
+// Runs up to kMidRun tails are sorted by one warp, longer ones by a CTA.
+constexpr int kMidRun = 1024;
+
 // Runs of 1..32 tails.  A warp takes 32 rows at a time, one per lane:
-// single-tail rows are written at once, runs of 2..32 are sorted one after
-// the other across the warp's registers (keys in lanes 0..L-1, +inf above),
-// longer runs are queued for k_runs_mid / k_runs_big.
+// single-tail rows are written at once, runs of 2..32 are sorted across the
+// warp's registers (keys in lanes 0..L-1, +inf above), kSmallGroup runs at
+// a time with the network sized to the longest of them.
+// Longer runs are queued: 33..kMidRun tails from the front of `big` for
+// k_runs_mid (count nbig[0]), more from its back for k_runs_big (count
+// nbig[1]); the two never meet, since there are at most n runs.
 template <class C>
 __global__ void k_runs_small(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
                              const int64_t* __restrict__ hptr, const uint64_t* __restrict__ slot, int64_t n,
@@ -199,40 +213,70 @@ __global__ void k_runs_small(const int64_t* __restrict__ row_ptr, const int64_t*
     for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; base < n;
          base += warps * 32) {
         const int64_t r = base + lane;
-        int64_t L = 0;
+        int64_t L = 0, p0 = 0, hs = 0, re = 0;
         if (r < n) {
-            L = hptr[r + 1] - hptr[r];
-            if (L == 1) emit_tail(r, hstart[r], row_ptr[r + 1], slot[hptr[r]], hnext, col, head, edge_tail);
-            else if (L > 32) big[atomicAdd(nbig, 1u)] = (int32_t)r;
+            p0 = hptr[r];
+            L = hptr[r + 1] - p0;
+            if (L >= 1 && L <= 32) {
+                hs = hstart[r];
+                re = row_ptr[r + 1];
+            }
+            if (L == 1) emit_tail(r, hs, re, slot[p0], hnext, col, head, edge_tail);
+            else if (L > kMidRun) big[n - 1 - (int64_t)atomicAdd(&nbig[1], 1u)] = (int32_t)r;
+            else if (L > 32) big[atomicAdd(&nbig[0], 1u)] = (int32_t)r;
         }
         unsigned todo = __ballot_sync(0xffffffffu, L >= 2 && L <= 32);
         while (todo) {
-            const int j = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int64_t rr = base + j;
-            const int64_t i0 = hptr[rr];
-            const int len = (int)(hptr[rr + 1] - i0);
-            uint64_t x = lane < len ? slot[i0 + lane] : ~0ull;
+            // up to V runs at once: their loads, networks (sized to the
+            // longest, padded with +inf) and cursor atomics overlap
+            constexpr int V = kSmallGroup;
+            int js[V], len[V], maxlen = 0;
+            uint64_t x[V];
+            int64_t h[V], e[V], hp[V];
 #pragma unroll
-            for (int k = 2; k <= 32; k <<= 1) {
-                const uint64_t y = shfl_xor64(x, k - 1);   // mirror step
-                const bool low = (lane & (k - 1)) < (k >> 1);
-                x = low ? (x < y ? x : y) : (x < y ? y : x);
-#pragma unroll
-                for (int jj = k >> 2; jj > 0; jj >>= 1) {
-                    const uint64_t z = shfl_xor64(x, jj);
-                    const bool lo2 = (lane & jj) == 0;
-                    x = lo2 ? (x < z ? x : z) : (x < z ? z : x);
+            for (int u = 0; u < V; ++u) {
+                js[u] = todo ? __ffs(todo) - 1 : -1;   // the same in every lane
+                todo &= todo - 1;
+                len[u] = 0;
+                x[u] = ~0ull;
+                h[u] = e[u] = 0;
+                if (js[u] >= 0) {
+                    len[u] = __shfl_sync(0xffffffffu, (int)L, js[u]);
+                    const int64_t i0 = __shfl_sync(0xffffffffu, p0, js[u]);
+                    h[u] = __shfl_sync(0xffffffffu, hs, js[u]);
+                    e[u] = __shfl_sync(0xffffffffu, re, js[u]);
+                    if (lane < len[u]) x[u] = slot[i0 + lane];
+                    maxlen = max(maxlen, len[u]);
                 }
             }
-            if (lane < len) emit_tail(rr, hstart[rr] + lane, row_ptr[rr + 1], x, hnext, col, head, edge_tail);
+            for (int k = 2; k <= 32 && (k >> 1) < maxlen; k <<= 1) {
+                const bool low = (lane & (k - 1)) < (k >> 1);
+#pragma unroll
+                for (int u = 0; u < V; ++u) {
+                    const uint64_t y = shfl_xor64(x[u], k - 1);   // mirror step
+                    x[u] = low ? (x[u] < y ? x[u] : y) : (x[u] < y ? y : x[u]);
+                }
+                for (int jj = k >> 2; jj > 0; jj >>= 1) {
+                    const bool lo2 = (lane & jj) == 0;
+#pragma unroll
+                    for (int u = 0; u < V; ++u) {
+                        const uint64_t z = shfl_xor64(x[u], jj);
+                        x[u] = lo2 ? (x[u] < z ? x[u] : z) : (x[u] < z ? z : x[u]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < V; ++u)
+                if (lane < len[u]) hp[u] = (int64_t)atomicAdd(&hnext[(int32_t)(x[u] >> 32)], (C)1);
+#pragma unroll
+            for (int u = 0; u < V; ++u)
+                if (lane < len[u]) write_tail(base + js[u], h[u] + lane, e[u], x[u], hp[u], col, head, edge_tail);
         }
     }
 }
 
-// Queued runs of 33..kMidRun tails: one warp per run, the network in the
-// warp's own shared region.
-constexpr int kMidRun = 1024;
+// Queued runs of 33..kMidRun tails (nbig[0] of them, at the front of
+// `big`): one warp per run, the network in the warp's own shared region.
 constexpr int kMidWarps = 4;
 
 template <class C>
@@ -244,13 +288,12 @@ k_runs_mid(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hsta
     __shared__ uint64_t sk[kMidWarps][kMidRun];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint64_t* key = sk[w];
-    const unsigned count = *nbig;
+    const unsigned count = nbig[0];
     const unsigned warps = gridDim.x * kMidWarps;
     for (unsigned q = blockIdx.x * kMidWarps + w; q < count; q += warps) {
         const int64_t r = big[q];
         const int64_t i0 = hptr[r];
         const int len = (int)(hptr[r + 1] - i0);
-        if (len > kMidRun) continue;
         for (int i = lane; i < len; i += 32) key[i] = slot[i0 + i];
         __syncwarp();
         int P = 1;
@@ -266,8 +309,9 @@ k_runs_mid(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hsta
     }
 }
 
-// Queued runs longer than kMidRun: one CTA per run, the network in shared
-// memory (up to kRunSmem keys) or in place in `slot`.
+// Queued runs longer than kMidRun (nbig[1] of them, at the back of `big`):
+// one CTA per run, the network in shared memory (up to kRunSmem keys) or in
+// place in `slot`.
 constexpr int kRunSmem = 4096;
 constexpr int kRunThreads = 512;
 
@@ -275,15 +319,14 @@ template <class C>
 __global__ void __launch_bounds__(kRunThreads)
 k_runs_big(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
            const int64_t* __restrict__ hptr, uint64_t* __restrict__ slot, const int32_t* __restrict__ big,
-           const unsigned int* __restrict__ nbig, C* __restrict__ hnext, int32_t* __restrict__ col,
+           const unsigned int* __restrict__ nbig, int64_t n, C* __restrict__ hnext, int32_t* __restrict__ col,
            tc_head* __restrict__ head, int64_t* __restrict__ edge_tail) {
     __shared__ uint64_t sk[kRunSmem];
-    const unsigned count = *nbig;
+    const unsigned count = nbig[1];
     for (unsigned q = blockIdx.x; q < count; q += gridDim.x) {
-        const int64_t r = big[q];
+        const int64_t r = big[n - 1 - (int64_t)q];
         const int64_t i0 = hptr[r];
         const int len = (int)(hptr[r + 1] - i0);
-        if (len <= kMidRun) continue;   // the same for every thread of the CTA
         uint64_t* key = len <= kRunSmem ? sk : slot + i0;
         if (len <= kRunSmem)
             for (int i = threadIdx.x; i < len; i += blockDim.x) sk[i] = slot[i0 + i];
@@ -463,8 +506,8 @@ tc_status build_runs(tc_graph* g, cudaStream_t s, int64_t m, int64_t n, int bits
     }
     {
         launch_scope ls("build_runs_big", s);
-        k_runs_big<<<sm_count() * 2, kRunThreads, 0, s>>>(g->row_ptr, g->hstart, hptr, slot, big, nbig, hnext,
-                                                          g->col, g->head, g->edge_tail);
+        k_runs_big<<<sm_count() * 2, kRunThreads, 0, s>>>(g->row_ptr, g->hstart, hptr, slot, big, nbig, n,
+                                                          hnext, g->col, g->head, g->edge_tail);
         TC_LAUNCH_CHECK();
     }
     return TC_OK;
@@ -653,12 +696,12 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
         TC_TRY(sc.get(&slot, m));
         TC_TRY(sc.get(&dh, n + 1));
         TC_TRY(sc.get(&big, n + 1));
-        TC_TRY(sc.get(&nbig, 1));
+        TC_TRY(sc.get(&nbig, 2));
         TC_TRY(sc.get((uint8_t**)&hnext, (n + 1) * (narrow ? 4 : 8)));
         TC_TRY(sc.get((uint8_t**)&tnext, (n + 1) * (narrow ? 4 : 8)));
         TC_TRY(sc.get(&hptr, n + 1));
         TC_CUDA(cudaMemsetAsync(dh, 0, (n + 1) * 4, s));
-        TC_CUDA(cudaMemsetAsync(nbig, 0, 4, s));
+        TC_CUDA(cudaMemsetAsync(nbig, 0, 8, s));
         {
             launch_scope ls("build_edge_rank_keys", s);
             k_edge_rank_keys<<<grid_for(m), kThreads, 0, s>>>(g->edge_u, g->edge_v, rank, m, bits, keys, dh);
