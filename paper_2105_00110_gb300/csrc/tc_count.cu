@@ -792,8 +792,8 @@ __global__ void k_classify(const int64_t* __restrict__ row_ptr, const int64_t* _
                 // on a warp (bitmap or list)
                 const bool heavy = W >= pp.cta_min_work && W >= 2 * words;
                 if (hv <= kThreadMaxH && lv + W <= kThreadMaxWork) c = TC_CLS_THREAD;
-                else if (heavy && !warp_bm && cta_s) c = TC_CLS_BITMAP_S;
-                else if (heavy && !warp_bm && cta_l) c = TC_CLS_BITMAP_L;
+                else if (heavy && cta_s) c = TC_CLS_BITMAP_S;
+                else if (heavy && cta_l) c = TC_CLS_BITMAP_L;
                 else if (warp_bm || warp_list) c = TC_CLS_WARP;
                 else if (cta_s) c = TC_CLS_BITMAP_S;
                 else if (cta_l) c = TC_CLS_BITMAP_L;
