@@ -271,3 +271,30 @@ def test_upload_timed_not_counted():
     assert launches == 1 and ms > 0
     assert "copy_h2d_pairs" not in profs[1]
     assert {k: v[0] for k, v in profs[0].items() if k != "copy_h2d_pairs"} == {k: v[0] for k, v in profs[1].items()}
+
+
+@pytest.mark.parametrize("strategy", ["auto", "bitmap", "global"])
+def test_runs_of_every_length_closed_form(strategy):
+    # K_k in rank space has a run of every length 0 .. k-1, so the build
+    # sorts runs on both sides of each tier boundary (32, 1024, and the
+    # in-place sort above 4096); closed forms check every output
+    k = 4200
+    s, d, n = gg.complete_graph(k)
+    g = tcg.Graph(torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), n)
+    try:
+        g.set_strategy(strategy)
+        tri, flags, total, _ = g.count()
+        numer, tcv, den, _ = g.centrality()
+        eu, ev = g.edges()
+        tri2, et, total2, _ = g.edge_triangles()
+        torch.cuda.synchronize()
+        c2 = (k - 1) * (k - 2) // 2
+        assert total == total2 == k * c2 // 3 and den == 3 * total
+        assert torch.all(tri.view(torch.int64) == c2) and torch.equal(tri2.view(torch.int64), tri.view(torch.int64))
+        assert torch.all(flags == 1) and torch.all(et.view(torch.int32) == k - 2)
+        assert torch.all(numer.view(torch.int64) == k * c2)
+        assert torch.all(tcv == 1.0)
+        iu = np.triu_indices(k, 1)
+        assert np.array_equal(eu.cpu().numpy(), iu[0]) and np.array_equal(ev.cpu().numpy(), iu[1])
+    finally:
+        g.close()
