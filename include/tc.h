@@ -229,9 +229,31 @@ typedef struct {
     double  class_head[5];       /* head entries (lower neighbours) of each class       */
     double  count_bytes;         /* algorithmic DRAM bytes of the whole count step      */
     double  centrality_bytes;    /* algorithmic DRAM bytes of the gather + divide step  */
+    int64_t core_vertices;       /* C of the dense core (0: none): the top C ranks,
+                                    whose mutual triangles come from one matrix product;
+                                    the counts above then leave that work out           */
 } tc_graph_stats;
 
 tc_status tc_get_stats(const tc_graph* g, tc_graph_stats* out);
+
+/*
+ * Dense core of the count step (an implementation choice, no counterpart in
+ * the paper; results never change).  Among the highest ranks of the degree
+ * order (Lemma 1's orientation puts the hubs last) the adjacency is dense,
+ * and every triangle whose lowest vertex is among the top C ranks lies there
+ * entirely.  For such a core tc_count takes those triangles from the product
+ * A_c·A_c on the tensor cores (cuBLAS, bf16 0/1 operands, fp32 sums, exact
+ * for C <= 2^24) masked by A_c, which is the matrix form T = A² ∘ A of the
+ * section "Notation" restricted to the core; the sparse kernels skip them.
+ *
+ * Process-wide setting read by later tc_build_csr calls: c = -1 (default)
+ * lets each build choose C in {4096, 8192, 16384} when the product is
+ * expected to be faster than streaming the core's rows (else no core); c = 0
+ * never; c > 0 uses the top min(c, n) ranks.  Batches never use a core.
+ * The product needs C²·6 bytes of device memory during tc_count.
+ * Returns TC_ERR_INVALID_ARG for c < -1.
+ */
+tc_status tc_set_dense_core(long long c);
 
 /* Force one intersection strategy for later tc_count calls on g. */
 tc_status tc_set_strategy(tc_graph* g, int strategy);

@@ -39,7 +39,8 @@ TC_STRATEGY_GLOBAL = 4
 STRATEGIES = {"auto": 0, "bsearch": 1, "merge": 2, "bitmap": 3, "global": 4}
 
 EXPORTED = ["tc_build_csr", "tc_count", "tc_count_shard", "tc_load_counts", "tc_edge_triangles", "tc_centrality", "tc_divide", "tc_graph_info",
-            "tc_copy_edges", "tc_get_stats", "tc_set_strategy", "tc_set_plan_params", "tc_get_plan_params", "tc_profile_enable",
+            "tc_copy_edges", "tc_get_stats", "tc_set_strategy", "tc_set_plan_params", "tc_get_plan_params",
+            "tc_set_dense_core", "tc_profile_enable",
             "tc_profile_reset", "tc_profile_read", "tc_launch_count", "tc_graph_free",
             "tc_status_str", "tc_batch_build", "tc_batch_run", "tc_batch_info",
             "tc_batch_copy_edges", "tc_batch_get_stats", "tc_batch_autotune", "tc_batch_get_params",
@@ -66,7 +67,8 @@ class GraphStats(ctypes.Structure):
                 ("avg_degeneracy", ctypes.c_double),
                 ("items", ctypes.c_int64 * 5), ("class_bytes", ctypes.c_double * 5),
                 ("class_wedges", ctypes.c_double * 5), ("class_head", ctypes.c_double * 5),
-                ("count_bytes", ctypes.c_double), ("centrality_bytes", ctypes.c_double)]
+                ("count_bytes", ctypes.c_double), ("centrality_bytes", ctypes.c_double),
+                ("core_vertices", ctypes.c_int64)]
 
     def as_dict(self):
         d = {}
@@ -126,6 +128,8 @@ def lib():
         L.tc_get_plan_params.argtypes = [vp, vp]
         L.tc_set_strategy.restype = i32
         L.tc_set_strategy.argtypes = [vp, i32]
+        L.tc_set_dense_core.restype = i32
+        L.tc_set_dense_core.argtypes = [ctypes.c_longlong]
         L.tc_profile_enable.restype = i32
         L.tc_profile_enable.argtypes = [i32]
         L.tc_profile_reset.restype = i32
@@ -327,6 +331,12 @@ def tc_set_strategy(g, strategy):
 def tc_set_plan_params(g, cta_min_work: int, cta_chunk: int, warp_chunk: int):
     arr = (ctypes.c_int64 * 3)(int(cta_min_work), int(cta_chunk), int(warp_chunk))
     _check(lib().tc_set_plan_params(g, arr), "tc_set_plan_params", ok=(TC_OK,))
+
+
+def tc_set_dense_core(c: int):
+    """Process-wide dense-core setting for later builds: -1 chooses per graph
+    (default), 0 never, c > 0 the top min(c, n) ranks."""
+    _check(lib().tc_set_dense_core(int(c)), "tc_set_dense_core", ok=(TC_OK,))
 
 
 def tc_get_plan_params(g):

@@ -2,12 +2,14 @@
 ``paper_2105_00110_gb300/_build/libtc_gb300.so`` for sm_103a (GB300).
 
 nvcc cross-compiles without a GPU.  Translation units are compiled in
-parallel and linked with the CUDA runtime statically, so the library needs
-no runtime search path.
+parallel and linked with the CUDA runtime statically; cuBLAS is linked
+dynamically from the toolkit, whose lib64 the library records as its run
+path.
 """
 from __future__ import annotations
 
 import os
+import shutil
 import subprocess
 import sys
 
@@ -17,9 +19,11 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtc_gb300.so")
-SOURCES = ["tc_api.cu", "tc_build.cu", "tc_count.cu", "tc_gather.cu", "tc_batch.cu", "tc_noalloc.cu", "tc_server.cu"]
+SOURCES = ["tc_api.cu", "tc_build.cu", "tc_count.cu", "tc_core.cu", "tc_gather.cu", "tc_batch.cu", "tc_noalloc.cu",
+           "tc_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+
 
 
 def _nvcc() -> str:
@@ -27,6 +31,18 @@ def _nvcc() -> str:
         if cand and (os.path.sep not in cand or os.path.exists(cand)):
             return cand
     return "nvcc"
+
+
+def _link_flags() -> list:
+    """cuBLAS (the dense core's matrix product) from the toolkit of nvcc,
+    with that lib64 as the library's run path."""
+    nv = _nvcc()
+    path = nv if os.path.sep in nv else shutil.which(nv)
+    if path:
+        lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(path))), "lib64")
+        if os.path.isdir(lib):
+            return ["-L" + lib, "-Xlinker", "-rpath," + lib, "-lcublas"]
+    return ["-lcublas"]
 
 
 def _stale() -> bool:
@@ -61,7 +77,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed for " + ", ".join(failed))
     tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call([nvcc, *ARCH, "-shared", *objs, "-o", tmp])
+    subprocess.check_call([nvcc, *ARCH, "-shared", *objs, *_link_flags(), "-o", tmp])
     os.replace(tmp, LIB)
     return LIB
 

@@ -328,6 +328,7 @@ tc_status tc_copy_edges(const tc_graph* g, int32_t* d_u, int32_t* d_v, tc_stream
 tc_status tc_get_stats(const tc_graph* g, tc_graph_stats* out) {
     if (!g || !out) return TC_ERR_INVALID_ARG;
     *out = g->stats;
+    out->core_vertices = g->core_c;
     return TC_OK;
 }
 

@@ -193,7 +193,7 @@ tc_status build_batch(tc_batch* b, const void* src, const void* dst, const int64
         return TC_ERR_OUT_OF_MEMORY;
     }
     cudaGetDevice(&b->g->device);
-    B_TRY(build_graph(b->g, gs, gd, np, n, TC_IN_DEVICE | TC_IDS_INT32, s));
+    B_TRY(build_graph(b->g, gs, gd, np, n, TC_IN_DEVICE | TC_IDS_INT32 | TC_BUILD_NO_CORE, s));
     tc_graph* g = b->g;
     B_TRY(dalloc((void**)&b->rank_graph, (n + 1) * 4, s));
     if (n > 0) {

@@ -142,12 +142,14 @@ __global__ void k_tail_place(const uint64_t* __restrict__ keys, int64_t m, int b
 // {r, |{w ∈ N_H(r) : w > hi}| = e - t - 1, twin = t}.
 __device__ __forceinline__ void write_tail(int64_t r, int64_t t, int64_t e, uint64_t x, int64_t hp,
                                            int32_t* __restrict__ col, tc_head* __restrict__ head,
-                                           int64_t* __restrict__ edge_tail) {
+                                           int64_t* __restrict__ edge_tail, int64_t core_t) {
     col[t] = (int32_t)(x >> 32);
     edge_tail[x & 0xffffffffull] = t;
     tc_head rec;
     rec.u = (int32_t)r;
-    rec.hrem = (int32_t)(e - t - 1);
+    // a lower end in the dense core (ranks >= core_t) streams nothing: the
+    // core's product counts those triangles
+    rec.hrem = r >= core_t ? 0 : (int32_t)(e - t - 1);
     rec.twin = t;
     head[hp] = rec;   // one 16-byte store
 }
@@ -155,9 +157,9 @@ __device__ __forceinline__ void write_tail(int64_t r, int64_t t, int64_t e, uint
 template <class C>
 __device__ __forceinline__ void emit_tail(int64_t r, int64_t t, int64_t e, uint64_t x, C* __restrict__ hnext,
                                           int32_t* __restrict__ col, tc_head* __restrict__ head,
-                                          int64_t* __restrict__ edge_tail) {
+                                          int64_t* __restrict__ edge_tail, int64_t core_t) {
     const int64_t hp = (int64_t)atomicAdd(&hnext[(int32_t)(x >> 32)], (C)1);
-    write_tail(r, t, e, x, hp, col, head, edge_tail);
+    write_tail(r, t, e, x, hp, col, head, edge_tail, core_t);
 }
 
 // Short runs handled together by one warp in k_runs_small.
@@ -207,7 +209,7 @@ __global__ void k_runs_small(const int64_t* __restrict__ row_ptr, const int64_t*
                              const int64_t* __restrict__ hptr, const uint64_t* __restrict__ slot, int64_t n,
                              C* __restrict__ hnext, int32_t* __restrict__ col, tc_head* __restrict__ head,
                              int64_t* __restrict__ edge_tail, int32_t* __restrict__ big,
-                             unsigned int* __restrict__ nbig) {
+                             unsigned int* __restrict__ nbig, int64_t core_t) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t base = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; base < n;
@@ -221,7 +223,7 @@ __global__ void k_runs_small(const int64_t* __restrict__ row_ptr, const int64_t*
                 hs = hstart[r];
                 re = row_ptr[r + 1];
             }
-            if (L == 1) emit_tail(r, hs, re, slot[p0], hnext, col, head, edge_tail);
+            if (L == 1) emit_tail(r, hs, re, slot[p0], hnext, col, head, edge_tail, core_t);
             else if (L > kMidRun) big[n - 1 - (int64_t)atomicAdd(&nbig[1], 1u)] = (int32_t)r;
             else if (L > 32) big[atomicAdd(&nbig[0], 1u)] = (int32_t)r;
         }
@@ -270,7 +272,7 @@ __global__ void k_runs_small(const int64_t* __restrict__ row_ptr, const int64_t*
                 if (lane < len[u]) hp[u] = (int64_t)atomicAdd(&hnext[(int32_t)(x[u] >> 32)], (C)1);
 #pragma unroll
             for (int u = 0; u < V; ++u)
-                if (lane < len[u]) write_tail(base + js[u], h[u] + lane, e[u], x[u], hp[u], col, head, edge_tail);
+                if (lane < len[u]) write_tail(base + js[u], h[u] + lane, e[u], x[u], hp[u], col, head, edge_tail, core_t);
         }
     }
 }
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(32 * kMidWarps)
 k_runs_mid(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
            const int64_t* __restrict__ hptr, const uint64_t* __restrict__ slot, const int32_t* __restrict__ big,
            const unsigned int* __restrict__ nbig, C* __restrict__ hnext, int32_t* __restrict__ col,
-           tc_head* __restrict__ head, int64_t* __restrict__ edge_tail) {
+           tc_head* __restrict__ head, int64_t* __restrict__ edge_tail, int64_t core_t) {
     __shared__ uint64_t sk[kMidWarps][kMidRun];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint64_t* key = sk[w];
@@ -304,7 +306,7 @@ k_runs_mid(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hsta
                 __syncwarp();
             }
         const int64_t h = hstart[r], e = row_ptr[r + 1];
-        for (int i = lane; i < len; i += 32) emit_tail(r, h + i, e, key[i], hnext, col, head, edge_tail);
+        for (int i = lane; i < len; i += 32) emit_tail(r, h + i, e, key[i], hnext, col, head, edge_tail, core_t);
         __syncwarp();
     }
 }
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(kRunThreads)
 k_runs_big(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
            const int64_t* __restrict__ hptr, uint64_t* __restrict__ slot, const int32_t* __restrict__ big,
            const unsigned int* __restrict__ nbig, int64_t n, C* __restrict__ hnext, int32_t* __restrict__ col,
-           tc_head* __restrict__ head, int64_t* __restrict__ edge_tail) {
+           tc_head* __restrict__ head, int64_t* __restrict__ edge_tail, int64_t core_t) {
     __shared__ uint64_t sk[kRunSmem];
     const unsigned count = nbig[1];
     for (unsigned q = blockIdx.x; q < count; q += gridDim.x) {
@@ -339,7 +341,7 @@ k_runs_big(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hsta
                 __syncthreads();
             }
         const int64_t h = hstart[r], e = row_ptr[r + 1];
-        for (int i = threadIdx.x; i < len; i += blockDim.x) emit_tail(r, h + i, e, key[i], hnext, col, head, edge_tail);
+        for (int i = threadIdx.x; i < len; i += blockDim.x) emit_tail(r, h + i, e, key[i], hnext, col, head, edge_tail, core_t);
         __syncthreads();
     }
 }
@@ -481,7 +483,7 @@ tc_status sort_keys(scratch& sc, cub::DoubleBuffer<T>& buf, int64_t count, int e
 template <class C>
 tc_status build_runs(tc_graph* g, cudaStream_t s, int64_t m, int64_t n, int bits, const uint64_t* keys,
                      uint64_t* slot, const int32_t* dh, const int64_t* hptr, int32_t* big, unsigned int* nbig,
-                     C* hnext, C* tnext, int rows_blocks) {
+                     C* hnext, C* tnext, int rows_blocks, int64_t core_t) {
     {
         launch_scope ls("build_hstart", s);
         k_hstart<<<grid_for(n), kThreads, 0, s>>>(g->row_ptr, dh, hptr, n, g->hstart, hnext, tnext);
@@ -495,19 +497,19 @@ tc_status build_runs(tc_graph* g, cudaStream_t s, int64_t m, int64_t n, int bits
     {
         launch_scope ls("build_runs_small", s);
         k_runs_small<<<rows_blocks, kThreads, 0, s>>>(g->row_ptr, g->hstart, hptr, slot, n, hnext, g->col,
-                                                      g->head, g->edge_tail, big, nbig);
+                                                      g->head, g->edge_tail, big, nbig, core_t);
         TC_LAUNCH_CHECK();
     }
     {
         launch_scope ls("build_runs_mid", s);
         k_runs_mid<<<sm_count() * 8, 32 * kMidWarps, 0, s>>>(g->row_ptr, g->hstart, hptr, slot, big, nbig, hnext,
-                                                             g->col, g->head, g->edge_tail);
+                                                             g->col, g->head, g->edge_tail, core_t);
         TC_LAUNCH_CHECK();
     }
     {
         launch_scope ls("build_runs_big", s);
         k_runs_big<<<sm_count() * 2, kRunThreads, 0, s>>>(g->row_ptr, g->hstart, hptr, slot, big, nbig, n,
-                                                          hnext, g->col, g->head, g->edge_tail);
+                                                          hnext, g->col, g->head, g->edge_tail, core_t);
         TC_LAUNCH_CHECK();
     }
     return TC_OK;
@@ -719,12 +721,15 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
         }
         const int cap = sm_count() * 16;
         const int rows_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, cap));
+        // the dense core, if one pays: its rows' head records stream nothing
+        TC_TRY(core_setup(g, dh, flags, s));
+        const int64_t core_t = n - g->core_c;
         if (narrow) {
             TC_TRY(build_runs(g, s, m, n, bits, keys, slot, dh, hptr, big, nbig, (uint32_t*)hnext,
-                              (uint32_t*)tnext, rows_blocks));
+                              (uint32_t*)tnext, rows_blocks, core_t));
         } else {
             TC_TRY(build_runs(g, s, m, n, bits, keys, slot, dh, hptr, big, nbig, (unsigned long long*)hnext,
-                              (unsigned long long*)tnext, rows_blocks));
+                              (unsigned long long*)tnext, rows_blocks, core_t));
         }
     } else if (n > 0) {
         // no edges: every row is empty

@@ -1097,10 +1097,14 @@ tc_status run_count(tc_graph* g, cudaStream_t s, bool edge_counts, int shard, in
     TC_CUDA(cudaMemsetAsync(g->tri, 0, (n + 1) * 8, s));
     TC_CUDA(cudaMemsetAsync(g->flag, 0, flag_words(e2) * 4, s));
     TC_CUDA(cudaMemsetAsync(g->counters, 0, 8 * 8, s));
-    if (!edge_counts) return launch_count_kernels<false>(g, s, g->flag, shard, num_shards);
+    if (!edge_counts) {
+        TC_TRY(launch_count_kernels<false>(g, s, g->flag, shard, num_shards));
+        return shard == 0 ? run_core(g, s, false) : TC_OK;   // the core's triangles, once
+    }
     if (!g->ecnt) TC_TRY(dalloc((void**)&g->ecnt, (e2 + 1) * 4, s));
     TC_CUDA(cudaMemsetAsync(g->ecnt, 0, (e2 + 1) * 4, s));
     TC_TRY(launch_count_kernels<true>(g, s, g->ecnt, shard, num_shards));
+    if (shard == 0) TC_TRY(run_core(g, s, true));
     if (e2 > 0) {
         launch_scope ls("count_edges_flags", s);
         const int64_t words = (e2 + 31) >> 5;

@@ -100,6 +100,10 @@ struct tc_graph {
     tc_plan_params params;
     int plan_params_version = 0, params_version = 0;
     tc_graph_stats stats{};
+    // dense core: the top core_c ranks, whose mutual triangles the count
+    // takes from one matrix product (0: none; the head entries of a core
+    // row whose lower end is in the core then stream nothing)
+    int64_t core_c = 0;
     // optional per-graph denominators (batches): rank -> graph, Σ△(v) per graph
     const int32_t* rank_graph = nullptr;
     const unsigned long long* den_graph = nullptr;
@@ -169,6 +173,17 @@ int sm_count();
 tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np, int64_t n,
                       uint32_t flags, cudaStream_t s);
 void free_graph_memory(tc_graph* g);
+
+// dense core (tc_core.cu).  Build flag for unions of many graphs, which
+// have no dense core: the build never sets one up.
+constexpr uint32_t TC_BUILD_NO_CORE = 1u << 30;
+// Chooses the core (g->core_c) from d_H of the top ranks (dh, device),
+// before the head records are written: those whose lower end is in the core
+// get stream length 0.
+tc_status core_setup(tc_graph* g, const int32_t* dh, uint32_t flags, cudaStream_t s);
+// Adds the core's triangles: △ of its vertices, △(G), and flags (or, with
+// edge counts, t(u, v)) of its edges.
+tc_status run_core(tc_graph* g, cudaStream_t s, bool edge_counts);
 
 // count (tc_count.cu)
 tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s);
