@@ -378,7 +378,7 @@ def run_ours(args, spec, wl_name):
         core_c = stats.get("core_vertices") or 0
         if core_c and "count_core_gemm" in kern:
             launch_n, tot_ms = kern["count_core_gemm"]
-            flop = 2.0 * float(core_c) ** 3
+            flop = float(stats.get("core_flop") or 2.0 * float(core_c) ** 3)
             ach = flop / (tot_ms / launch_n / 1e3) / 1e12
             tpk, tkind = bf16_peak()
             core_roof = {"kernel": "count_core_gemm", "bound": "tensor", "achieved": round(ach, 1), "peak": tpk,

@@ -232,6 +232,8 @@ typedef struct {
     int64_t core_vertices;       /* C of the dense core (0: none): the top C ranks,
                                     whose mutual triangles come from one matrix product;
                                     the counts above then leave that work out           */
+    double  core_flop;           /* tensor FLOP of that product per count (the blocks of
+                                    A_c·A_c the masked pass reads)                      */
 } tc_graph_stats;
 
 tc_status tc_get_stats(const tc_graph* g, tc_graph_stats* out);

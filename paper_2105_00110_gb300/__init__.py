@@ -68,7 +68,7 @@ class GraphStats(ctypes.Structure):
                 ("items", ctypes.c_int64 * 5), ("class_bytes", ctypes.c_double * 5),
                 ("class_wedges", ctypes.c_double * 5), ("class_head", ctypes.c_double * 5),
                 ("count_bytes", ctypes.c_double), ("centrality_bytes", ctypes.c_double),
-                ("core_vertices", ctypes.c_int64)]
+                ("core_vertices", ctypes.c_int64), ("core_flop", ctypes.c_double)]
 
     def as_dict(self):
         d = {}

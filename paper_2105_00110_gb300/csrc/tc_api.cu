@@ -176,6 +176,10 @@ void note_launch(const char* name, cudaStream_t s, int phase, bool counts) {
 
 }  // namespace tcx
 
+namespace tcx {
+double core_flop(int64_t C);   // tc_core.cu
+}
+
 using namespace tcx;
 
 extern "C" {
@@ -329,6 +333,7 @@ tc_status tc_get_stats(const tc_graph* g, tc_graph_stats* out) {
     if (!g || !out) return TC_ERR_INVALID_ARG;
     *out = g->stats;
     out->core_vertices = g->core_c;
+    out->core_flop = g->core_c > 0 ? tcx::core_flop(g->core_c) : 0.0;
     return TC_OK;
 }
 

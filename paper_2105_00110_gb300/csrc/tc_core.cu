@@ -43,7 +43,9 @@ constexpr int64_t kCoreMax = 16384;
 // Rough rates of the two ways to count the core's triangles, used only to
 // decide whether the dense product pays: ids streamed per ms by the bitmap
 // count kernel, bf16 tensor FLOP per ms of a cuBLAS GEMM, and the bytes per
-// ms of the fill and the masked pass over M.
+// ms of the fill and the masked pass over M.  Both are below what R-MAT
+// scale 24 showed (about 1.0e9 core ids/ms saved, 2.2e12 FLOP/ms), so the
+// rule errs towards streaming.
 constexpr double kStreamIdsPerMs = 0.7e9;
 constexpr double kGemmFlopPerMs = 1.5e12;
 constexpr double kPassBytesPerMs = 4.0e9;
@@ -135,17 +137,49 @@ tc_status blas_on(cudaStream_t s, cublasHandle_t* out) {
     return TC_OK;
 }
 
-cudaError_t core_gemm(cublasHandle_t h, int64_t C, const uint16_t* A, float* M) {
+// The masked pass reads M only at (j, i) with j > i in column-major order
+// (core edge i < j), so M is computed by blocks: with C split into B blocks
+// of bs, the B(B+1)/2 blocks (R, K) with R >= K, each A_c[R, :]·A_c[:, K]
+// (one batched call).  B = 1 is the whole product.
+int core_blocks(int64_t C) { return (C >= 2048 && C % 8 == 0) ? 8 : 1; }
+
+__global__ void k_core_ptrs(const uint16_t* A, float* M, int64_t C, int B, const void** pa, const void** pb,
+                            void** pm) {
+    const int64_t bs = C / B;
+    int q = 0;
+    for (int K = 0; K < B; ++K)
+        for (int R = K; R < B; ++R, ++q)
+            if (q == (int)threadIdx.x) {
+                pa[q] = A + R * bs;              // rows R of A_c (column-major, leading dimension C)
+                pb[q] = A + K * bs * C;          // columns K
+                pm[q] = M + K * bs * C + R * bs; // block (R, K) of M
+            }
+}
+
+cudaError_t core_gemm(cublasHandle_t h, int64_t C, const uint16_t* A, float* M, const void** pa, const void** pb,
+                      void** pm) {
     const float one = 1.0f, zero = 0.0f;
-    const int c = (int)C;
-    // A_c is symmetric, so storage order does not matter: M = A_c · A_c
-    const cublasStatus_t st = cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, c, c, c, &one, A, CUDA_R_16BF, c, A,
-                                           CUDA_R_16BF, c, &zero, M, CUDA_R_32F, c, CUBLAS_COMPUTE_32F,
-                                           CUBLAS_GEMM_DEFAULT);
+    const int c = (int)C, B = core_blocks(C);
+    cublasStatus_t st;
+    if (B == 1) {
+        // A_c is symmetric, so storage order does not matter: M = A_c · A_c
+        st = cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, c, c, c, &one, A, CUDA_R_16BF, c, A, CUDA_R_16BF, c, &zero,
+                          M, CUDA_R_32F, c, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+    } else {
+        const int bs = c / B;
+        st = cublasGemmBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_N, bs, bs, c, &one, pa, CUDA_R_16BF, c, pb, CUDA_R_16BF,
+                                 c, &zero, pm, CUDA_R_32F, c, B * (B + 1) / 2, CUBLAS_COMPUTE_32F,
+                                 CUBLAS_GEMM_DEFAULT);
+    }
     return st == CUBLAS_STATUS_SUCCESS ? cudaSuccess : cudaErrorUnknown;
 }
 
 }  // namespace
+
+double core_flop(int64_t C) {
+    const int B = core_blocks(C);
+    return 2.0 * (double)C * C * C * (B * (B + 1) / 2) / ((double)B * B);
+}
 
 tc_status core_setup(tc_graph* g, const int32_t* dh, uint32_t flags, cudaStream_t s) {
     g->core_c = 0;
@@ -165,7 +199,7 @@ tc_status core_setup(tc_graph* g, const int32_t* dh, uint32_t flags, cudaStream_
             if (c > n) break;
             double wedges = 0;   // Σ C(d_H, 2) over the top c ranks: ids the core's rows stream
             for (int64_t i = top - c; i < top; ++i) wedges += 0.5 * (double)h[i] * (double)(h[i] - 1);
-            const double cost = 2.0 * (double)c * c * c / kGemmFlopPerMs + 8.0 * (double)c * c / kPassBytesPerMs;
+            const double cost = core_flop(c) / kGemmFlopPerMs + 8.0 * (double)c * c / kPassBytesPerMs;
             const double gain = wedges / kStreamIdsPerMs - cost;
             if (gain > best) {
                 best = gain;
@@ -183,9 +217,12 @@ tc_status run_core(tc_graph* g, cudaStream_t s, bool edge_counts) {
     uint16_t* A = nullptr;
     float* M = nullptr;
     ull* S = nullptr;
+    void** P = nullptr;   // the batched call's pointer arrays (A rows, A columns, M blocks)
+    const int B = core_blocks(C), nb = B * (B + 1) / 2;
     TC_TRY(dalloc((void**)&A, (size_t)C * C * 2, s));
     tc_status st = dalloc((void**)&M, (size_t)C * C * 4, s);
     if (st == TC_OK) st = dalloc((void**)&S, (size_t)(C + 1) * 8, s);
+    if (st == TC_OK) st = dalloc((void**)&P, (size_t)3 * nb * sizeof(void*), s);
     if (st == TC_OK) {
         st = [&]() -> tc_status {
             TC_CUDA(cudaMemsetAsync(A, 0, (size_t)C * C * 2, s));
@@ -195,17 +232,25 @@ tc_status run_core(tc_graph* g, cudaStream_t s, bool edge_counts) {
                 k_core_fill<<<warp_blocks(C), kCoreThreads, 0, s>>>(g->row_ptr, g->hstart, g->col, t, C, A);
                 TC_LAUNCH_CHECK();
             }
+            const void** pa = (const void**)P;
+            const void** pb = (const void**)(P + nb);
+            void** pm = P + 2 * nb;
+            if (B > 1) {
+                launch_scope ls("count_core_ptrs", s);
+                k_core_ptrs<<<1, nb, 0, s>>>(A, M, C, B, pa, pb, pm);
+                TC_LAUNCH_CHECK();
+            }
             cublasHandle_t h = nullptr;
             TC_TRY(blas_on(s, &h));
             {
                 launch_scope ls("count_core_gemm", s);
-                const int64_t k = library_kernels("core_gemm", C, 0, [&](cudaStream_t p) {
+                const int64_t k = library_kernels("core_gemm", C, B, [&](cudaStream_t p) {
                     cublasHandle_t hp = nullptr;
                     if (blas_on(p, &hp) != TC_OK) return cudaErrorUnknown;
-                    return core_gemm(hp, C, A, M);
+                    return core_gemm(hp, C, A, M, pa, pb, pm);
                 });
                 TC_TRY(blas_on(s, &h));
-                TC_CUDA(core_gemm(h, C, A, M));
+                TC_CUDA(core_gemm(h, C, A, M, pa, pb, pm));
                 add_launches(k - 1);
             }
             {
@@ -224,6 +269,7 @@ tc_status run_core(tc_graph* g, cudaStream_t s, bool edge_counts) {
             return TC_OK;
         }();
     }
+    if (P) dfree(P, s);
     if (S) dfree(S, s);
     if (M) dfree(M, s);
     dfree(A, s);
