@@ -61,6 +61,12 @@ def test_host_argument_checks_reject_without_device(built):
     assert lib.tc_centrality(None, None, None, None, None) == tcg.TC_ERR_INVALID_ARG
     assert lib.tc_set_strategy(None, 0) == tcg.TC_ERR_INVALID_ARG
     assert lib.tc_divide(None, -1, 3, None, None) == tcg.TC_ERR_INVALID_ARG
+    # dense-core setting: host only; the build flag that keeps unions of
+    # graphs without a core is not a public flag
+    assert lib.tc_set_dense_core(-2) == tcg.TC_ERR_INVALID_ARG
+    for c in (0, 4096, -1):
+        assert lib.tc_set_dense_core(c) == tcg.TC_OK
+    assert lib.tc_build_csr(None, None, 0, 5, 1 << 30, None, ctypes.byref(h)) == tcg.TC_ERR_INVALID_ARG
 
 
 def test_no_cpu_fallback():
