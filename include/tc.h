@@ -382,8 +382,13 @@ void tc_batch_free(tc_batch* b);
  * the limits, odd nnz or NULL inputs; TC_ERR_CUDA if the address lookup or
  * a launch fails; otherwise TC_OK once the work is enqueued on `stream`
  * (not synchronised; △(G) = 0 is not reported here).  An input that breaks
- * the CSR rules above is detected on the device: every d_tri and d_numer
- * entry is then UINT64_MAX and every d_tc entry NaN.
+ * the CSR rules above (an id out of range, an unsorted or repeated row
+ * entry, a self loop, an entry u in row v without v in row u, bad row
+ * offsets) is detected on the device: every d_tri and d_numer entry is
+ * then UINT64_MAX and every d_tc entry NaN.  d_tc alone cannot tell that
+ * case from a triangle-free graph (NaN everywhere too): pass d_tri, which
+ * is all zero for a valid triangle-free graph and all UINT64_MAX for a
+ * rejected input.
  */
 #define TC_NOALLOC_MAX_VERTICES 65536
 #define TC_NOALLOC_MAX_ENTRIES 2097152

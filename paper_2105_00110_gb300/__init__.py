@@ -294,10 +294,32 @@ def tc_csr_centrality_noalloc(row_ptr, col, n: int, tri=None, numer=None, tc=Non
     (row_ptr [n+1] int64, col [nnz] int32; sorted, symmetric, no loops),
     using only the library's fixed working array: nothing is allocated.
     Outputs are caller tensors (tri/numer uint64 [n], tc float64 [n]).
-    Calls on one device must not overlap in time."""
-    for t, dt in ((row_ptr, torch.int64), (col, torch.int32)):
+    Calls on one device must not overlap in time.
+
+    Every argument is checked here, before the library sees a pointer: a
+    wrong length, dtype or device would make the kernels read or write out
+    of bounds, which the C entry point cannot detect."""
+    n = int(n)
+    if n < 0:
+        raise ValueError("n must be non-negative")
+    checks = [("row_ptr", row_ptr, torch.int64, n + 1), ("col", col, torch.int32, None),
+              ("tri", tri, torch.uint64, n), ("numer", numer, torch.uint64, n), ("tc", tc, torch.float64, n)]
+    dev = torch.cuda.current_device() if torch.cuda.is_available() else None
+    for name, t, dt, size in checks:
+        if t is None:
+            if name in ("row_ptr", "col"):
+                raise ValueError("%s is required" % name)
+            continue
+        if not isinstance(t, torch.Tensor) or t.dim() != 1:
+            raise ValueError("%s must be a 1-D tensor" % name)
         if t.dtype != dt:
-            raise ValueError("row_ptr must be int64 and col int32")
+            raise ValueError("%s must be %s, got %s" % (name, dt, t.dtype))
+        if size is not None and t.numel() != size:
+            raise ValueError("%s must hold %d entries, got %d" % (name, size, t.numel()))
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError("%s must be on the current CUDA device (cuda:%s)" % (name, dev))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
     st = lib().tc_csr_centrality_noalloc(_dptr(row_ptr), _dptr(col) if col.numel() else None, int(n),
                                          col.numel(), _dptr(tri), _dptr(numer), _dptr(tc),
                                          _stream(stream))

@@ -8,6 +8,7 @@ path.
 """
 from __future__ import annotations
 
+import json
 import os
 import shutil
 import subprocess
@@ -19,6 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtc_gb300.so")
+BUILD_INFO = os.path.join(BUILD, "build_info.json")
 SOURCES = ["tc_api.cu", "tc_build.cu", "tc_count.cu", "tc_core.cu", "tc_gather.cu", "tc_batch.cu", "tc_noalloc.cu",
            "tc_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -77,8 +79,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed for " + ", ".join(failed))
     tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.check_call([nvcc, *ARCH, "-shared", *objs, *_link_flags(), "-o", tmp])
+    link = [nvcc, *ARCH, "-shared", *objs, *_link_flags(), "-o", tmp]
+    subprocess.check_call(link)
     os.replace(tmp, LIB)
+    # the commands this library was made with (read by the build checks)
+    with open(BUILD_INFO, "w") as fh:
+        json.dump({"compile": [[nvcc, *ARCH, *FLAGS, "-c", src] for src in SOURCES], "link": link[:-2]}, fh)
     return LIB
 
 

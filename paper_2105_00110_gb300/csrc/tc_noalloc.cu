@@ -169,9 +169,12 @@ __global__ void k_na_count(na_args a) {
 
 // One warp per vertex v: numer(v) = △(v) + Σ_{u∈N(v)} (flag ? 1 : 3)·△(u),
 // with the flag of (v, u) at position p of row v if u > v, else at the
-// position of v in row u (a missing reverse entry means the CSR is not
-// symmetric).  Then TC(v) = numer(v) / 3△(G): both operands stay below
-// 2^53 within the size limits, so one IEEE division is correctly rounded.
+// position of v in row u.  Every entry u of row v, above or below v, has
+// its reverse entry v looked up in row u: a missing one means the CSR is
+// not symmetric, which the count pass alone cannot see (it only follows
+// entries above their row).  Then TC(v) = numer(v) / 3△(G): both operands
+// stay below 2^53 within the size limits, so one IEEE division is
+// correctly rounded.
 __global__ void k_na_gather(na_args a, ull* d_tri, ull* d_numer, double* d_tc) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -187,19 +190,17 @@ __global__ void k_na_gather(na_args a, ull* d_tri, ull* d_numer, double* d_tc) {
                 bad = true;
                 continue;
             }
-            int64_t pos = p;
-            if (u < v) {
-                int64_t ub, ue;
-                if (!na_row(a, u, ub, ue)) {
-                    bad = true;
-                    continue;
-                }
-                pos = na_find(a.col, ub, ue, (int32_t)v);
-                if (pos < 0) {
-                    bad = true;
-                    continue;
-                }
+            int64_t ub, ue;
+            if (!na_row(a, u, ub, ue)) {
+                bad = true;
+                continue;
             }
+            const int64_t back = na_find(a.col, ub, ue, (int32_t)v);   // v's entry in row u
+            if (back < 0) {
+                bad = true;
+                continue;
+            }
+            const int64_t pos = u > v ? p : back;   // the edge's flag sits in its lower end's row
             acc += (na_flag_get(a, pos) ? 1ull : 3ull) * a.tri[u];
         }
         if (bad) na_fail(a);

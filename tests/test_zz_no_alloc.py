@@ -146,3 +146,58 @@ def test_unsorted_row_is_reported_in_the_outputs():
     got = noalloc(torch.from_numpy(row_ptr).cuda(), torch.from_numpy(col).cuda(), n)
     ref = existing_path(s, d, n)
     assert all(same(a, b) for a, b in zip(got, ref))
+
+
+def test_one_sided_upper_entry_is_reported_in_the_outputs():
+    # rows {1, 2, 3}, {2}, {}, {}: entries above their row whose reverse
+    # entry is missing (row 1 lacks 0, row 2 lacks 0 and 1, row 3 lacks 0)
+    row_ptr = torch.tensor([0, 3, 4, 4, 4], dtype=torch.int64, device="cuda")
+    col = torch.tensor([1, 2, 3, 2], dtype=torch.int32, device="cuda")
+    tri, numer, tc = noalloc(row_ptr, col, 4)
+    torch.cuda.synchronize()
+    assert (tri.cpu().numpy().view(np.int64) == -1).all()
+    assert (numer.cpu().numpy().view(np.int64) == -1).all()
+    assert np.isnan(tc.cpu().numpy()).all()
+    # one missing reverse entry in an otherwise valid graph: K_5 with row 4
+    # lacking 3 (its rows stay sorted and nnz stays even by dropping 0 from row 3 too)
+    s, d, n = gg.complete_graph(5)
+    rp, cl = csr_of(s, d, n)
+    rows = [list(cl[rp[i]:rp[i + 1]]) for i in range(n)]
+    rows[4].remove(3)
+    rows[3].remove(0)
+    rp2 = np.zeros(n + 1, np.int64)
+    np.cumsum([len(r) for r in rows], out=rp2[1:])
+    cl2 = np.concatenate([np.asarray(r, np.int32) for r in rows])
+    tri, numer, tc = noalloc(torch.from_numpy(rp2).cuda(), torch.from_numpy(cl2).cuda(), n)
+    torch.cuda.synchronize()
+    assert (tri.cpu().numpy().view(np.int64) == -1).all()
+    assert np.isnan(tc.cpu().numpy()).all()
+
+
+def test_triangle_free_graph_is_told_apart_from_a_rejected_one():
+    tree = (np.arange(1, 50, dtype=np.int32), (np.arange(1, 50) // 2).astype(np.int32), 50)
+    row_ptr, col = csr_of(*tree)
+    tri, numer, tc = noalloc(torch.from_numpy(row_ptr).cuda(), torch.from_numpy(col).cuda(), 50)
+    torch.cuda.synchronize()
+    assert (tri.cpu().numpy() == 0).all() and np.isnan(tc.cpu().numpy()).all()
+
+
+def test_wrapper_rejects_bad_outputs_before_the_call():
+    s, d, n = gg.complete_graph(6)
+    row_ptr, col = csr_of(s, d, n)
+    rp, cl = torch.from_numpy(row_ptr).cuda(), torch.from_numpy(col).cuda()
+    u64 = lambda k: torch.zeros(k, dtype=torch.int64, device="cuda").view(torch.uint64)
+    bad = [
+        dict(row_ptr=rp[:-1], col=cl, n=n),                                        # row_ptr too short
+        dict(row_ptr=rp, col=cl.view(1, -1), n=n),                                 # col not 1-D
+        dict(row_ptr=rp, col=cl, n=n, tri=u64(n - 1)),                             # tri too short
+        dict(row_ptr=rp, col=cl, n=n, numer=torch.zeros(n, dtype=torch.int64, device="cuda")),  # not uint64
+        dict(row_ptr=rp, col=cl, n=n, tc=torch.zeros(n, dtype=torch.float32, device="cuda")),   # float32
+        dict(row_ptr=rp, col=cl, n=n, tc=torch.zeros(n, dtype=torch.float64)),     # host memory
+        dict(row_ptr=rp.cpu(), col=cl, n=n),                                       # host memory
+    ]
+    before = tcg.tc_launch_count()
+    for kw in bad:
+        with pytest.raises(ValueError):
+            tcg.tc_csr_centrality_noalloc(**kw)
+    assert tcg.tc_launch_count() == before
