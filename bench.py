@@ -64,18 +64,6 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def bf16_peak():
-    """Dense bf16 tensor peak for the core's product: a few ms of tensor
-    work inside a memory-bound step, so the measured burst cuBLAS figure
-    (the sustained one holds for seconds of back-to-back GEMMs under the
-    power cap), else the fallback."""
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return float(json.load(fh)["bf16_tflops"]), "measured burst"
-    except Exception:
-        return 1900.0, "fallback"
-
-
 # ------------------------------------------------------- DRAM traffic
 COUNT_SOURCES = ["paper_2105_00110_gb300/csrc/tc_count.cu", "paper_2105_00110_gb300/csrc/tc_internal.cuh"]
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "count_dram_traffic_rmat24.md")
@@ -176,6 +164,17 @@ class ClockSampler:
                 "samples": len(use), "in_timed_region": bool(inside), "reasons": sorted(reasons)}
 
 
+def shard_exchange(tri, flags, group=None):
+    """The exchange step of a sharded count: the partial △(v) of every rank
+    summed and the edge flags OR-ed, in place (NCCL between GPUs, gloo on
+    CPU).  A single process has nothing to exchange."""
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size(group) == 1:
+        return tri, flags
+    import paper_2105_00110_gb300 as tcg
+    return tcg.allreduce_counts(tri, flags, group)
+
+
 def aggregate(t_ms: float, e2e_ms: float, units: int, e2e_units: int, world: int, device=None):
     """Whole-job figures across ranks: the slowest rank's time (MAX) and the
     units all ranks processed (SUM).  Identity for a single process."""
@@ -201,13 +200,14 @@ def run_ours(args, spec, wl_name):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     tcg.build()
 
-    src_np, dst_np, n = generate(spec, rank)
+    # sharded: every rank holds the same graph and counts its share of the
+    # work items; replicas: every rank its own graph
+    sharded = world > 1 and not getattr(args, "replicas", False)
+    src_np, dst_np, n = generate(spec, 0 if sharded else rank)
     np_pairs = len(src_np)
     d_src = torch.from_numpy(src_np).to(dev)
     d_dst = torch.from_numpy(dst_np).to(dev)
@@ -232,7 +232,13 @@ def run_ours(args, spec, wl_name):
         m = tcg.tc_graph_info(g)[1]
         if flag_buf[0] is None or flag_buf[0].numel() < m:
             flag_buf[0] = torch.empty(max(m, 1), dtype=torch.uint8, device=dev)
-        st, total = tcg.tc_count(g, tri, flag_buf[0][:max(m, 1)] if m else None, stream)
+        fl = flag_buf[0][:max(m, 1)] if m else None
+        if sharded:
+            tcg.tc_count_shard(g, rank, world, tri, fl, stream)
+            shard_exchange(tri, fl)
+            st, total = tcg.tc_load_counts(g, tri, fl, stream)
+        else:
+            st, total = tcg.tc_count(g, tri, fl, stream)
         t2 = time.perf_counter()
         tcg.tc_centrality(g, numer, tcv, stream)
         if to_host:
@@ -288,7 +294,7 @@ def run_ours(args, spec, wl_name):
     # ---------------- per-edge triangle counts: the count in edge-count mode
     # against the plain count, on one built graph (outside the timed step)
     edge_counts = None
-    if world == 1:
+    if world == 1 and getattr(args, "edge_counts", True):
         g = tcg.Graph(d_src, d_dst, n, stream)
         et = torch.empty(max(g.m, 1), dtype=torch.int32, device=dev).view(torch.uint32)
         times = {}
@@ -340,6 +346,8 @@ def run_ours(args, spec, wl_name):
     h2d_gbs = (2 * np_pairs * 4 / (upload_ms / 1e3) / 1e9) if upload_ms else None
 
     t_max, e2e_max, edges_all, e2e_edges_all = aggregate(t_ms, e2e_ms, edges, e2e_edges, world, dev)
+    if sharded:   # one graph for the whole job: its edges count once
+        edges_all, e2e_edges_all = edges, e2e_edges
 
     if rank == 0:
         peak, peak_kind = peaks()
@@ -373,18 +381,17 @@ def run_ours(args, spec, wl_name):
             survey_roof = {"model": "B_alg = 4*sum_u d_H(u)^2 + 43m + 64n per graph, t = count + centrality kernels",
                            "bytes": b_alg, "t_ms": round(t_cc, 3), "achieved": round(ach, 1), "peak": peak,
                            "unit": "GB/s", "frac": round(ach / peak, 4)}
-        # the dense core's product (tensor cores): 2 C^3 FLOP per count
-        core_roof = None
+        # the dense core's bit-packed pass: one AND + population count per
+        # 32-bit row word, core edges x words per row per count
+        core_obj = None
         core_c = stats.get("core_vertices") or 0
-        if core_c and "count_core_gemm" in kern:
-            launch_n, tot_ms = kern["count_core_gemm"]
-            flop = float(stats.get("core_flop") or 2.0 * float(core_c) ** 3)
-            ach = flop / (tot_ms / launch_n / 1e3) / 1e12
-            tpk, tkind = bf16_peak()
-            core_roof = {"kernel": "count_core_gemm", "bound": "tensor", "achieved": round(ach, 1), "peak": tpk,
-                         "peak_kind": tkind, "unit": "TFLOP/s", "frac": round(ach / tpk, 4),
-                         "flop_per_launch": flop, "core_vertices": core_c,
-                         "avg_launch_ms": round(tot_ms / launch_n, 4)}
+        if core_c and "count_core_pairs" in kern:
+            launch_n, tot_ms = kern["count_core_pairs"]
+            words = float(stats.get("core_words") or 0.0)
+            t_s = tot_ms / launch_n / 1e3
+            core_obj = {"kernel": "count_core_pairs", "core_vertices": core_c, "words_per_launch": words,
+                        "avg_launch_ms": round(tot_ms / launch_n, 4),
+                        "achieved_gwords_per_s": round(words / t_s / 1e9, 1) if t_s > 0 else None}
         cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu) else None
         line = {
             "metric": METRIC,
@@ -395,14 +402,17 @@ def run_ours(args, spec, wl_name):
             "warmup": args.warmup,
             "ms_per_step": step_ms,
             "higher_is_better": True,
-            "scaling": "weak",
+            "scaling": "strong" if sharded else "weak",
             "vs_baseline": None,
             "dtype": "int64",
             "data": "synthetic",
             "config": {"workload": wl_name, "n": n, "m": m, "pairs": np_pairs,
                        "generator": spec, "triangles": total,
                        "l2": "inputs larger than L2 (pair list %.1f GB per step)" % (np_pairs * 8 / 1e9),
-                       "parallelism": "replicas" if world > 1 else "single"},
+                       "parallelism": ("shard%d: every rank builds the graph, counts work items rank, "
+                                       "rank + N, ...; NCCL sum of counts and OR of flags; local gather"
+                                       % world) if sharded else ("replicas" if world > 1 else "single"),
+                       "backend": dist.get_backend() if world > 1 else None},
             "clocks": clocks,
             "e2e": {"value": e2e_edges_all / (e2e_max / 1e3), "unit": "edges/s",
                     "h2d_bytes_per_step": 2 * np_pairs * 4,
@@ -421,13 +431,12 @@ def run_ours(args, spec, wl_name):
             "phases_ms_per_step": kernel_ms,
             "count_plus_centrality_edges_per_s": (m / ((count_ms + gather_ms) / 1e3)) if count_ms else None,
             "roofline_survey_model": survey_roof,
-            "roofline_core_gemm": core_roof,
+            "dense_core": core_obj,
             "edge_triangles": edge_counts,
             "graph_stats": stats,
         }
-        print(json.dumps(line))
-    if world > 1:
-        dist.destroy_process_group()
+        return line
+    return None
 
 
 # ------------------------------------------------------------ batched path
@@ -444,8 +453,6 @@ def run_batched(args, spec, wl_name):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     tcg.build()
@@ -560,7 +567,7 @@ def run_batched(args, spec, wl_name):
                     "traffic": None, "algorithmic_bytes_per_launch": bytes_per[name],
                     "avg_launch_ms": round(tot / nl, 4)}
         value = edges_all / (t_max / 1e3)
-        print(json.dumps({
+        return {
             "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
@@ -580,9 +587,8 @@ def run_batched(args, spec, wl_name):
             "batched_speedup_vs_per_graph": value / per_graph_rate,
             "autotuned_params": tuned,
             "graph_stats": stats,
-        }))
-    if world > 1:
-        dist.destroy_process_group()
+        }
+    return None
 
 
 # ------------------------------------------------------------- served path
@@ -732,7 +738,7 @@ def run_served(args, spec, wl_name):
     sus = run_phase(sus_rate, spec["sustain_duration"], pool_seed + 2, drain=True)
     if rank == 0:
         n_done = max(over["completed"], 1)
-        print(json.dumps({
+        return {
             "metric": METRIC + "; p50/p99 request latency", "value": over["achieved_edges_per_s"],
             "unit": "edges/s", "n_gpus": 1, "steps": over["completed"], "warmup": len(pool),
             "ms_per_step": 1e3 * over["window_s"] / n_done, "higher_is_better": True,
@@ -750,56 +756,105 @@ def run_served(args, spec, wl_name):
             "gpu_launches": over["gpu_launches"], "roofline": None, "cpu_baseline": None,
             "latency_ms": over["latency_ms"],
             "overload": over, "sustainable": sus,
-        }))
+        }
+    return None
 
 
 # ------------------------------------------------------------- oracle side
-CPU_SAMPLE = dict(kind="rmat", scale=19, edge_factor=16, seed=0x5EED0012)
+CPU_SAMPLE_ALL = dict(kind="rmat", scale=22, edge_factor=16, seed=0x5EED0016)
+CPU_SAMPLE_ONE = dict(kind="rmat", scale=19, edge_factor=16, seed=0x5EED0012)
+REF_SAMPLE = dict(kind="rmat", scale=18, edge_factor=16, seed=0x5EED0010)
 
 
-def oracle_pass(spec):
-    """Full triangle centrality by the oracle; returns (edges, seconds)."""
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_pass(spec, threads=1):
+    """Full triangle centrality by the oracle (build, degree-ordered listing,
+    Definition 1 numerators, exact division) on `threads` host threads;
+    returns (edges, seconds)."""
     import oracle
     s, d, n = generate(spec)
     t0 = time.perf_counter()
-    r = oracle.run(s, d, n, "fast")
+    r = oracle.run(s, d, n, "fast", threads=threads, algebraic=False)
     dt = time.perf_counter() - t0
     return len(r["adj"]) // 2, dt
 
 
 def cpu_baseline(args):
-    m, dt = oracle_pass(CPU_SAMPLE)
-    return {"value": m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": "R-MAT scale 19, edge factor 16, same (a,b,c,d), full TC by the oracle "
-                      "(canonical CSR, degree-ordered listing, Definition 1 numerators, exact "
-                      "division), single thread, %.1f s" % dt}
+    cores = host_cores()
+    m_all, dt_all = oracle_pass(CPU_SAMPLE_ALL, cores)
+    m_one, dt_one = oracle_pass(CPU_SAMPLE_ONE, 1)
+    return {"value": m_all / dt_all, "unit": "edges/s", "cores": cores, "kind": "oracle",
+            "sample": "R-MAT scale 22, edge factor 16, same (a,b,c,d) as the workload: full TC by the oracle "
+                      "(canonical CSR, degree-ordered listing, Definition 1 numerators, exact division) "
+                      "on all %d host threads, %.1f s" % (cores, dt_all),
+            "single_thread": {"value": m_one / dt_one, "unit": "edges/s", "cores": 1,
+                              "sample": "R-MAT scale 19, same generator and oracle, one thread, %.1f s" % dt_one}}
 
 
 def run_reference(args, wl_name):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    spec = dict(kind="rmat", scale=16, edge_factor=16, seed=0x5EED0010)
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle_pass(spec)
+        oracle_pass(REF_SAMPLE, cores)
     tot_m, tot_t = 0, 0.0
     for _ in range(args.steps):
-        m, dt = oracle_pass(spec)
+        m, dt = oracle_pass(REF_SAMPLE, cores)
         tot_m += m
         tot_t += dt
     val = tot_m / tot_t
-    sample = ("each step: R-MAT scale 16, edge factor 16, same (a,b,c,d) as the workload, full "
-              "TC by the oracle, single thread (a bounded sample of %s)" % wl_name)
+    sample = ("each step: R-MAT scale 18, edge factor 16, same (a,b,c,d) as the workload, full "
+              "TC by the oracle on all %d host threads (a bounded sample of %s)" % (cores, wl_name))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": val, "unit": "edges/s",
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic", "config": {"workload": wl_name},
-        "cpu_baseline": {"value": val, "unit": "edges/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": val, "unit": "edges/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": val, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+# ----------------------------------------------------------- default suite
+def run_other_configs(args):
+    """The other four workloads of the suite, each measured in this process
+    with its own clock record, for the default run's "configs" key: R-MAT
+    scale 12 and the 4096^2 grid + Chung-Lu overlay (plain single graph),
+    the 8192-graph batch and the served Poisson stream."""
+    import torch
+    out = {}
+    small = argparse.Namespace(**vars(args))
+    small.no_cpu = True
+    small.edge_counts = False
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "e2e", "gpu_launches", "roofline", "clocks",
+            "phases_ms_per_step", "roofline_survey_model", "dense_core")
+    for name, steps in (("rmat-s12-ef16", max(args.steps, 20)), ("grid4096-diag05-cl21", args.steps)):
+        small.steps = steps
+        line = run_ours(small, WORKLOADS[name], name)
+        cfg = {k: line.get(k) for k in keep}
+        cfg["config"] = {k: line["config"][k] for k in ("n", "m", "pairs", "triangles")}
+        cfg["phases_ms_per_step"] = dict(list(line["phases_ms_per_step"].items())[:8])
+        out[name] = cfg
+        torch.cuda.empty_cache()
+    b = argparse.Namespace(**vars(args))
+    b.steps = 3
+    line = run_batched(b, BATCH_WORKLOADS["batched-8192"], "batched-8192")
+    line.pop("graph_stats", None)
+    line["phases_ms_per_step"] = dict(list(line["phases_ms_per_step"].items())[:8])
+    out["batched-8192"] = line
+    torch.cuda.empty_cache()
+    line = run_served(args, SERVED_WORKLOADS["served-poisson"], "served-poisson")
+    out["served-poisson"] = line
+    return out
 
 
 def main(argv=None):
@@ -807,22 +862,46 @@ def main(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(SERVED_WORKLOADS))
+    ap.add_argument("--workload", default=None,
+                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(SERVED_WORKLOADS),
+                    help="one workload alone (default: R-MAT scale 24, then the other four configs)")
     ap.add_argument("--baseline-graphs", type=int, default=8192,
                     help="graphs timed one launch per graph (batched workloads)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-configs", action="store_true", help="default run: skip the other four configs")
+    ap.add_argument("--replicas", action="store_true",
+                    help="under torchrun: every rank counts its own graph (default for single graphs: one "
+                         "graph sharded across the ranks)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    suite = args.workload is None
+    wl = args.workload or DEFAULT_WORKLOAD
     if args.impl == "reference":
-        run_reference(args, args.workload)
-    elif args.workload in SERVED_WORKLOADS:
-        run_served(args, SERVED_WORKLOADS[args.workload], args.workload)
-    elif args.workload in BATCH_WORKLOADS:
-        run_batched(args, BATCH_WORKLOADS[args.workload], args.workload)
+        run_reference(args, wl)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        # NCCL's communicator set-up lines (rank count, devices) on stderr
+        os.environ.setdefault("NCCL_DEBUG", "INFO")
+        os.environ.setdefault("NCCL_DEBUG_SUBSYS", "INIT")
+        os.environ.setdefault("NCCL_DEBUG_FILE", "/dev/stderr")
+        dist.init_process_group("nccl")
+    if wl in SERVED_WORKLOADS:
+        line = run_served(args, SERVED_WORKLOADS[wl], wl)
+    elif wl in BATCH_WORKLOADS:
+        line = run_batched(args, BATCH_WORKLOADS[wl], wl)
     else:
-        run_ours(args, WORKLOADS[args.workload], args.workload)
+        line = run_ours(args, WORKLOADS[wl], wl)
+    if suite and world == 1 and line is not None and not args.no_configs:
+        line["configs"] = run_other_configs(args)
+    if line is not None:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

@@ -59,7 +59,9 @@ typedef enum {
     TC_ERR_CUDA = -3,           /* any other CUDA runtime error               */
     TC_ERR_OVERFLOW = -4,       /* 3·△(G) does not fit in 64 bits             */
     TC_ERR_TIMEOUT = -5,        /* a bounded device-side wait gave up         */
-    TC_ERR_STATE = -6           /* call order violated (e.g. no tc_count yet) */
+    TC_ERR_STATE = -6,          /* call order violated (e.g. no tc_count yet) */
+    TC_ERR_BOUNDS = -7          /* bounds-checked builds only: a kernel's index
+                                   check failed (the access was skipped)      */
 } tc_status;
 
 /* tc_build_csr flags */
@@ -230,10 +232,11 @@ typedef struct {
     double  count_bytes;         /* algorithmic DRAM bytes of the whole count step      */
     double  centrality_bytes;    /* algorithmic DRAM bytes of the gather + divide step  */
     int64_t core_vertices;       /* C of the dense core (0: none): the top C ranks,
-                                    whose mutual triangles come from one matrix product;
-                                    the counts above then leave that work out           */
-    double  core_flop;           /* tensor FLOP of that product per count (the blocks of
-                                    A_c·A_c the masked pass reads)                      */
+                                    whose mutual triangles are counted edge by edge
+                                    from bit-packed core rows; the counts above then
+                                    leave that work out                                */
+    double  core_words;          /* 32-bit row words ANDed by that pass per count
+                                    (core edges x words per packed core row)          */
 } tc_graph_stats;
 
 tc_status tc_get_stats(const tc_graph* g, tc_graph_stats* out);
@@ -243,17 +246,20 @@ tc_status tc_get_stats(const tc_graph* g, tc_graph_stats* out);
  * the paper; results never change).  Among the highest ranks of the degree
  * order (Lemma 1's orientation puts the hubs last) the adjacency is dense,
  * and every triangle whose lowest vertex is among the top C ranks lies there
- * entirely.  For such a core tc_count takes those triangles from the product
- * A_c·A_c on the tensor cores (cuBLAS, bf16 0/1 operands, fp32 sums, exact
- * for C <= 2^24) masked by A_c, which is the matrix form T = A² ∘ A of the
- * section "Notation" restricted to the core; the sparse kernels skip them.
+ * entirely.  For such a core tc_count counts those triangles edge by edge:
+ * on each core edge (x, y), T(x, y) = |N_c(x) ∩ N_c(y)| is the AND and
+ * population count of the two bit-packed core rows — the matrix form
+ * T = A² ∘ A of the section "Notation" restricted to the core, evaluated
+ * only on its edges — and the sparse kernels skip those triangles.
  *
  * Process-wide setting read by later tc_build_csr calls: c = -1 (default)
- * lets each build choose C in {4096, 8192, 16384} when the product is
- * expected to be faster than streaming the core's rows (else no core); c = 0
- * never; c > 0 uses the top min(c, n) ranks.  Batches never use a core.
- * The product needs C²·6 bytes of device memory during tc_count.
- * Returns TC_ERR_INVALID_ARG for c < -1.
+ * lets each build choose C in {4096, 8192, 16384, 32768} when the bit-packed
+ * pass is expected to be faster than streaming the core's rows (else no
+ * core); c = 0 never; 0 < c <= 32768 uses the top min(c, n) ranks.  Batches
+ * never use a core.  A count with a core holds C·W·6 + 8·C bytes of device
+ * memory while it runs, W = ⌈C/32⌉ rounded up to 128, 256, 512 or 1024
+ * (48 MB at C = 16384).  Returns TC_ERR_INVALID_ARG for c < -1 or
+ * c > 32768.
  */
 tc_status tc_set_dense_core(long long c);
 
@@ -288,6 +294,22 @@ tc_status tc_profile_read(tc_kernel_time* out, int cap, int* count);
 
 /* Number of kernels this library has launched since load (all threads). */
 int64_t tc_launch_count(void);
+
+/*
+ * Testing aids for failure handling (no counterpart in the paper).
+ * tc_debug_fail_allocation(k) arms one injected failure: the device
+ * allocation the library requests k allocations from now (k = 0: the next
+ * one) fails as if the device were out of memory; k < 0 disarms.  The
+ * entry point that meets it frees what it had allocated and returns
+ * TC_ERR_OUT_OF_MEMORY, and the next call works normally.  Process-wide
+ * and shared by every thread (the server's workers included).
+ * tc_debug_allocations counts the device allocations requested since the
+ * library was loaded, tc_debug_live_allocations those currently held (by
+ * graphs, batches and calls in flight).
+ */
+tc_status tc_debug_fail_allocation(int64_t k);
+int64_t tc_debug_allocations(void);
+int64_t tc_debug_live_allocations(void);
 
 /* ------------------------------------------------------------------ batches
  * Many independent graphs processed as one: the batch is the disjoint union

@@ -38,7 +38,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fno-fast-math", "-ffp-contract=off",
-                               "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"])
+                               "-shared", "-fPIC", "-pthread", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -80,6 +80,19 @@ def _load():
             lib.og_div_rn_long.argtypes = [u64, u64]
             lib.og_tc.restype = None
             lib.og_tc.argtypes = [vp, i64, u64, vp]
+            ci = ctypes.c_int
+            lib.og_build_mt.restype = vp
+            lib.og_build_mt.argtypes = [vp, vp, i64, i64, ci]
+            lib.og_edge_triangles_mt.restype = None
+            lib.og_edge_triangles_mt.argtypes = [vp, vp, ci]
+            lib.og_fast_edge_triangles_mt.restype = ci
+            lib.og_fast_edge_triangles_mt.argtypes = [vp, vp, ci]
+            lib.og_vertex_triangles_mt.restype = ci
+            lib.og_vertex_triangles_mt.argtypes = [vp, vp, vp, ci]
+            lib.og_numer_definition_mt.restype = None
+            lib.og_numer_definition_mt.argtypes = [vp, vp, vp, vp, vp, vp, ci]
+            lib.og_tc_mt.restype = None
+            lib.og_tc_mt.argtypes = [vp, i64, u64, vp, ci]
             _lib = lib
     return _lib
 
@@ -91,13 +104,19 @@ def _p(a: np.ndarray):
 class OracleGraph:
     """Canonical simple undirected graph (rows ascending) held by the oracle."""
 
-    def __init__(self, src, dst, n: int):
+    def __init__(self, src, dst, n: int, threads: int = 1):
+        """threads > 1 runs the build and every routine of run() on that many
+        host threads (same results bit for bit; the CPU timing baseline)."""
         lib = _load()
+        self.threads = max(1, int(threads))
         src = np.ascontiguousarray(src, dtype=np.int32)
         dst = np.ascontiguousarray(dst, dtype=np.int32)
         if src.shape != dst.shape:
             raise ValueError("src/dst length mismatch")
-        h = lib.og_build(_p(src), _p(dst), len(src), int(n))
+        if self.threads > 1:
+            h = lib.og_build_mt(_p(src), _p(dst), len(src), int(n), self.threads)
+        else:
+            h = lib.og_build(_p(src), _p(dst), len(src), int(n))
         if not h:
             raise ValueError("oracle: vertex id outside [0, n) or out of memory")
         self._h = ctypes.c_void_p(h)
@@ -117,10 +136,15 @@ class OracleGraph:
 
     def edge_triangles(self, mode: str = "definition") -> np.ndarray:
         t = np.zeros(max(2 * self.m, 1), dtype=np.uint64)
+        mt = self.threads > 1
         if mode == "definition":
-            _load().og_edge_triangles(self._h, _p(t))
+            if mt:
+                _load().og_edge_triangles_mt(self._h, _p(t), self.threads)
+            else:
+                _load().og_edge_triangles(self._h, _p(t))
         elif mode == "fast":
-            rc = _load().og_fast_edge_triangles(self._h, _p(t))
+            rc = (_load().og_fast_edge_triangles_mt(self._h, _p(t), self.threads) if mt
+                  else _load().og_fast_edge_triangles(self._h, _p(t)))
             if rc != 0:
                 raise RuntimeError("og_fast_edge_triangles failed (%d)" % rc)
         else:
@@ -155,19 +179,24 @@ class OracleGraph:
             raise RuntimeError("og_sample_tri failed (%d)" % rc)
         return tri, rows[: int(deg.sum())]
 
-    def run(self, mode: str = "definition") -> dict:
+    def run(self, mode: str = "definition", algebraic: bool = True) -> dict:
         """Everything the path computes, in the caller's vertex labels.
 
         Keys: ptr, adj (canonical CSR), t (per adjacency entry), flag (t > 0,
         uint8), tri, total, numer (Definition 1 form), numer_alg (Proposition 2
         form), core, noncore, den (= 3 total), tc (binary64, NaN if den == 0).
+        algebraic=False skips the Proposition 2 cross-form (numer_alg and
+        den_alg are then None), which the CPU timing baseline leaves out.
         """
         lib = _load()
+        mt = self.threads
         t = self.edge_triangles(mode)
         tb = np.ascontiguousarray(t) if len(t) else np.zeros(1, dtype=np.uint64)
         n = self.n
         tri = np.zeros(max(n, 1), dtype=np.uint64)
-        if lib.og_vertex_triangles(self._h, _p(tb), _p(tri)) != 0:
+        rc = (lib.og_vertex_triangles_mt(self._h, _p(tb), _p(tri), mt) if mt > 1
+              else lib.og_vertex_triangles(self._h, _p(tb), _p(tri)))
+        if rc != 0:
             raise AssertionError("odd row sum of T")
         rem = ctypes.c_uint64()
         total = int(lib.og_total(self._h, _p(tri), ctypes.byref(rem)))
@@ -176,22 +205,31 @@ class OracleGraph:
         numer = np.zeros(max(n, 1), dtype=np.uint64)
         core = np.zeros(max(n, 1), dtype=np.uint64)
         noncore = np.zeros(max(n, 1), dtype=np.uint64)
-        lib.og_numer_definition(self._h, _p(tb), _p(tri), _p(numer), _p(core), _p(noncore))
-        numer_alg = np.zeros(max(n, 1), dtype=np.uint64)
-        den_alg = ctypes.c_uint64()
-        if lib.og_numer_algebraic(self._h, _p(tb), _p(numer_alg), ctypes.byref(den_alg)) != 0:
-            raise AssertionError("odd algebraic numerator")
+        if mt > 1:
+            lib.og_numer_definition_mt(self._h, _p(tb), _p(tri), _p(numer), _p(core), _p(noncore), mt)
+        else:
+            lib.og_numer_definition(self._h, _p(tb), _p(tri), _p(numer), _p(core), _p(noncore))
+        numer_alg = den_alg = None
+        if algebraic:
+            numer_alg = np.zeros(max(n, 1), dtype=np.uint64)
+            d = ctypes.c_uint64()
+            if lib.og_numer_algebraic(self._h, _p(tb), _p(numer_alg), ctypes.byref(d)) != 0:
+                raise AssertionError("odd algebraic numerator")
+            numer_alg, den_alg = numer_alg[:n], int(d.value)
         den = 3 * total
         tc = np.zeros(max(n, 1), dtype=np.float64)
-        lib.og_tc(_p(numer), n, den, _p(tc))
+        if mt > 1:
+            lib.og_tc_mt(_p(numer), n, den, _p(tc), mt)
+        else:
+            lib.og_tc(_p(numer), n, den, _p(tc))
         return dict(ptr=self.ptr, adj=self.adj, t=t, flag=(t > 0).astype(np.uint8),
-                    tri=tri[:n], total=total, numer=numer[:n], numer_alg=numer_alg[:n],
-                    den_alg=int(den_alg.value), core=core[:n], noncore=noncore[:n],
+                    tri=tri[:n], total=total, numer=numer[:n], numer_alg=numer_alg,
+                    den_alg=den_alg, core=core[:n], noncore=noncore[:n],
                     den=den, tc=tc[:n])
 
 
-def run(src, dst, n: int, mode: str = "definition") -> dict:
-    return OracleGraph(src, dst, n).run(mode)
+def run(src, dst, n: int, mode: str = "definition", threads: int = 1, algebraic: bool = True) -> dict:
+    return OracleGraph(src, dst, n, threads).run(mode, algebraic)
 
 
 def div_rn(a: int, b: int) -> float:

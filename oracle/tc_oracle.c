@@ -423,3 +423,256 @@ double og_div_rn(uint64_t a, uint64_t b) {
 void og_tc(const uint64_t* numer, int64_t n, uint64_t den, double* out) {
     for (int64_t v = 0; v < n; ++v) out[v] = og_div_rn(numer[v], den);
 }
+
+/* ------------------------------------------------------------------ */
+/* The same routines spread over host threads (CPU timing baseline).    */
+/* ------------------------------------------------------------------ */
+/* Each *_mt routine below computes exactly what its single-threaded
+ * namesake computes: the outer loop over vertices is cut into chunks that
+ * POSIX threads take in turn, the work per vertex is the same statements,
+ * and where two vertices add into one entry (the three edges of a listed
+ * triangle) the addition is atomic.  Integer addition in any order gives
+ * the same sum, so the outputs are equal bit for bit (the tests check it).
+ * They exist only to time the oracle on all host cores. */
+#include <pthread.h>
+
+typedef struct {
+    int64_t n, chunk;
+    int64_t next;               /* next chunk start (atomic) */
+    void* ctx;
+    void (*body)(void* ctx, int64_t lo, int64_t hi);
+} og_pool;
+
+static void* og_worker(void* arg) {
+    og_pool* p = (og_pool*)arg;
+    for (;;) {
+        int64_t lo = __atomic_fetch_add(&p->next, p->chunk, __ATOMIC_RELAXED);
+        if (lo >= p->n) break;
+        int64_t hi = lo + p->chunk < p->n ? lo + p->chunk : p->n;
+        p->body(p->ctx, lo, hi);
+    }
+    return NULL;
+}
+
+/* body(ctx, lo, hi) over [0, n) in chunks, on `threads` threads (the caller
+ * is one of them). */
+static void og_parallel(int64_t n, int threads, void* ctx, void (*body)(void*, int64_t, int64_t)) {
+    if (threads < 1) threads = 1;
+    if (threads > 256) threads = 256;
+    og_pool p = {n, 256, 0, ctx, body};
+    pthread_t th[256];
+    int ok[256];
+    for (int k = 1; k < threads; ++k) ok[k] = pthread_create(&th[k], NULL, og_worker, &p) == 0;
+    og_worker(&p);
+    for (int k = 1; k < threads; ++k)
+        if (ok[k]) pthread_join(th[k], NULL);
+}
+
+/* og_build with the per-row sort and de-duplication on threads. */
+typedef struct {
+    int32_t* buf;
+    const int64_t* cnt;
+    int64_t* len;
+    int32_t* adj;
+    const int64_t* ptr;
+} og_build_ctx;
+
+static void og_build_rows(void* c, int64_t lo, int64_t hi) {
+    og_build_ctx* x = (og_build_ctx*)c;
+    for (int64_t v = lo; v < hi; ++v) {
+        int64_t b = x->cnt[v], e = x->cnt[v + 1], out = b;
+        qsort(x->buf + b, (size_t)(e - b), sizeof(int32_t), og_cmp_i32);
+        for (int64_t i = b; i < e; ++i)
+            if (i == b || x->buf[i] != x->buf[i - 1]) x->buf[out++] = x->buf[i];
+        x->len[v] = out - b;
+    }
+}
+
+static void og_build_copy(void* c, int64_t lo, int64_t hi) {
+    og_build_ctx* x = (og_build_ctx*)c;
+    for (int64_t v = lo; v < hi; ++v)
+        memcpy(x->adj + x->ptr[v], x->buf + x->cnt[v], sizeof(int32_t) * (size_t)(x->ptr[v + 1] - x->ptr[v]));
+}
+
+og_graph* og_build_mt(const int32_t* src, const int32_t* dst, int64_t np, int64_t n, int threads) {
+    if (n < 0 || np < 0 || n > INT32_MAX) return NULL;
+    for (int64_t i = 0; i < np; ++i)
+        if (src[i] < 0 || dst[i] < 0 || src[i] >= n || dst[i] >= n) return NULL;
+    int64_t* cnt = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!cnt) return NULL;
+    for (int64_t i = 0; i < np; ++i)
+        if (src[i] != dst[i]) { cnt[src[i] + 1] += 1; cnt[dst[i] + 1] += 1; }
+    for (int64_t v = 0; v < n; ++v) cnt[v + 1] += cnt[v];
+    int64_t total = cnt[n];
+    int32_t* buf = (int32_t*)malloc(sizeof(int32_t) * (size_t)(total + 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t* len = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    og_graph* g = (og_graph*)calloc(1, sizeof(og_graph));
+    if (!buf || !fill || !len || !g) { free(cnt); free(buf); free(fill); free(len); free(g); return NULL; }
+    memcpy(fill, cnt, sizeof(int64_t) * (size_t)(n + 1));
+    for (int64_t i = 0; i < np; ++i) {
+        if (src[i] == dst[i]) continue;
+        buf[fill[src[i]]++] = dst[i];
+        buf[fill[dst[i]]++] = src[i];
+    }
+    free(fill);
+    og_build_ctx x = {buf, cnt, len, NULL, NULL};
+    og_parallel(n, threads, &x, og_build_rows);
+    g->n = n;
+    g->ptr = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!g->ptr) { free(cnt); free(buf); free(len); free(g); return NULL; }
+    for (int64_t v = 0; v < n; ++v) g->ptr[v + 1] = g->ptr[v] + len[v];
+    g->adj = (int32_t*)malloc(sizeof(int32_t) * (size_t)(g->ptr[n] + 1));
+    if (!g->adj) { free(cnt); free(buf); free(len); free(g->ptr); free(g); return NULL; }
+    x.adj = g->adj;
+    x.ptr = g->ptr;
+    og_parallel(n, threads, &x, og_build_copy);
+    g->m = g->ptr[n] / 2;
+    free(cnt);
+    free(buf);
+    free(len);
+    return g;
+}
+
+/* og_edge_triangles on threads (every entry is its own merge). */
+typedef struct { const og_graph* g; uint64_t* t; } og_t_ctx;
+
+static void og_edge_rows(void* c, int64_t lo, int64_t hi) {
+    og_t_ctx* x = (og_t_ctx*)c;
+    for (int64_t v = lo; v < hi; ++v)
+        for (int64_t p = x->g->ptr[v]; p < x->g->ptr[v + 1]; ++p) x->t[p] = og_common(x->g, v, x->g->adj[p]);
+}
+
+void og_edge_triangles_mt(const og_graph* g, uint64_t* t, int threads) {
+    og_t_ctx x = {g, t};
+    og_parallel(g->n, threads, &x, og_edge_rows);
+}
+
+/* og_fast_edge_triangles on threads: the listing from each v in parallel
+ * (atomic additions), then the mirror entries in parallel. */
+typedef struct {
+    const og_graph* g;
+    uint64_t* t;
+    const int64_t* hptr;
+    const int64_t* hp;
+    int bad;
+} og_fast_ctx;
+
+static void og_fast_list(void* c, int64_t lo, int64_t hi) {
+    og_fast_ctx* x = (og_fast_ctx*)c;
+    const og_graph* g = x->g;
+    const int64_t* hptr = x->hptr;
+    const int64_t* hp = x->hp;
+    for (int64_t v = lo; v < hi; ++v) {
+        for (int64_t a = hptr[v]; a < hptr[v + 1]; ++a) {
+            int64_t puv = hp[a];
+            int32_t u = g->adj[puv];
+            int64_t i = hptr[v], j = hptr[u];
+            while (i < hptr[v + 1] && j < hptr[u + 1]) {
+                int32_t wi = g->adj[hp[i]], wj = g->adj[hp[j]];
+                if (wi < wj) ++i;
+                else if (wi > wj) ++j;
+                else {
+                    __atomic_fetch_add(&x->t[puv], 1, __ATOMIC_RELAXED);    /* edge {v,u} */
+                    __atomic_fetch_add(&x->t[hp[i]], 1, __ATOMIC_RELAXED);  /* edge {v,w} */
+                    __atomic_fetch_add(&x->t[hp[j]], 1, __ATOMIC_RELAXED);  /* edge {u,w} */
+                    ++i; ++j;
+                }
+            }
+        }
+    }
+}
+
+static void og_fast_mirror(void* c, int64_t lo, int64_t hi) {
+    og_fast_ctx* x = (og_fast_ctx*)c;
+    for (int64_t v = lo; v < hi; ++v)
+        for (int64_t a = x->hptr[v]; a < x->hptr[v + 1]; ++a) {
+            int64_t p = x->hp[a];
+            int64_t q = og_find(x->g, x->g->adj[p], (int32_t)v);
+            if (q < 0) { __atomic_store_n(&x->bad, 1, __ATOMIC_RELAXED); continue; }
+            x->t[q] = x->t[p];
+        }
+}
+
+int og_fast_edge_triangles_mt(const og_graph* g, uint64_t* t, int threads) {
+    int64_t n = g->n, e2 = 2 * g->m;
+    memset(t, 0, sizeof(uint64_t) * (size_t)(e2 ? e2 : 1));
+    int64_t* hptr = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t* hp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(g->m + 1));
+    if (!hptr || !hp) { free(hptr); free(hp); return -2; }
+    int64_t k = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        hptr[v] = k;
+        for (int64_t p = g->ptr[v]; p < g->ptr[v + 1]; ++p)
+            if (og_before(g, v, g->adj[p])) hp[k++] = p;
+    }
+    hptr[n] = k;
+    og_fast_ctx x = {g, t, hptr, hp, 0};
+    og_parallel(n, threads, &x, og_fast_list);
+    og_parallel(n, threads, &x, og_fast_mirror);
+    free(hptr);
+    free(hp);
+    return x.bad ? -1 : 0;
+}
+
+/* og_vertex_triangles, og_numer_definition and og_tc on threads (each
+ * vertex writes only its own entries). */
+typedef struct {
+    const og_graph* g;
+    const uint64_t* t;
+    const uint64_t* tri;
+    uint64_t* out;
+    uint64_t* core;
+    uint64_t* noncore;
+    int bad;
+} og_v_ctx;
+
+static void og_tri_rows(void* c, int64_t lo, int64_t hi) {
+    og_v_ctx* x = (og_v_ctx*)c;
+    for (int64_t v = lo; v < hi; ++v) {
+        uint64_t s = 0;
+        for (int64_t p = x->g->ptr[v]; p < x->g->ptr[v + 1]; ++p) s += x->t[p];
+        if (s & 1u) __atomic_store_n(&x->bad, 1, __ATOMIC_RELAXED);
+        x->out[v] = s / 2;
+    }
+}
+
+int og_vertex_triangles_mt(const og_graph* g, const uint64_t* t, uint64_t* tri, int threads) {
+    og_v_ctx x = {g, t, NULL, tri, NULL, NULL, 0};
+    og_parallel(g->n, threads, &x, og_tri_rows);
+    return x.bad ? -1 : 0;
+}
+
+static void og_numer_rows(void* c, int64_t lo, int64_t hi) {
+    og_v_ctx* x = (og_v_ctx*)c;
+    const og_graph* g = x->g;
+    for (int64_t v = lo; v < hi; ++v) {
+        uint64_t cx = x->tri[v], y = 0;
+        for (int64_t p = g->ptr[v]; p < g->ptr[v + 1]; ++p) {
+            int32_t u = g->adj[p];
+            if (x->t[p] > 0) cx += x->tri[u];
+            else y += x->tri[u];
+        }
+        x->out[v] = cx + 3 * y;
+        if (x->core) x->core[v] = cx;
+        if (x->noncore) x->noncore[v] = y;
+    }
+}
+
+void og_numer_definition_mt(const og_graph* g, const uint64_t* t, const uint64_t* tri, uint64_t* numer,
+                            uint64_t* core, uint64_t* noncore, int threads) {
+    og_v_ctx x = {g, t, tri, numer, core, noncore, 0};
+    og_parallel(g->n, threads, &x, og_numer_rows);
+}
+
+typedef struct { const uint64_t* numer; uint64_t den; double* out; } og_tc_ctx;
+
+static void og_tc_rows(void* c, int64_t lo, int64_t hi) {
+    og_tc_ctx* x = (og_tc_ctx*)c;
+    for (int64_t v = lo; v < hi; ++v) x->out[v] = og_div_rn(x->numer[v], x->den);
+}
+
+void og_tc_mt(const uint64_t* numer, int64_t n, uint64_t den, double* out, int threads) {
+    og_tc_ctx x = {numer, den, out};
+    og_parallel(n, threads, &x, og_tc_rows);
+}

@@ -27,6 +27,7 @@ TC_ERR_CUDA = -3
 TC_ERR_OVERFLOW = -4
 TC_ERR_TIMEOUT = -5
 TC_ERR_STATE = -6
+TC_ERR_BOUNDS = -7
 
 TC_IN_DEVICE = 1
 TC_IDS_INT32 = 2
@@ -45,7 +46,8 @@ EXPORTED = ["tc_build_csr", "tc_count", "tc_count_shard", "tc_load_counts", "tc_
             "tc_status_str", "tc_batch_build", "tc_batch_run", "tc_batch_info",
             "tc_batch_copy_edges", "tc_batch_get_stats", "tc_batch_autotune", "tc_batch_get_params",
             "tc_batch_free", "tc_csr_centrality_noalloc",
-            "tc_server_create", "tc_server_submit", "tc_server_poll", "tc_server_stats", "tc_server_free"]
+            "tc_server_create", "tc_server_submit", "tc_server_poll", "tc_server_stats", "tc_server_free",
+            "tc_debug_fail_allocation", "tc_debug_allocations", "tc_debug_live_allocations"]
 
 
 class TCError(RuntimeError):
@@ -68,7 +70,7 @@ class GraphStats(ctypes.Structure):
                 ("items", ctypes.c_int64 * 5), ("class_bytes", ctypes.c_double * 5),
                 ("class_wedges", ctypes.c_double * 5), ("class_head", ctypes.c_double * 5),
                 ("count_bytes", ctypes.c_double), ("centrality_bytes", ctypes.c_double),
-                ("core_vertices", ctypes.c_int64), ("core_flop", ctypes.c_double)]
+                ("core_vertices", ctypes.c_int64), ("core_words", ctypes.c_double)]
 
     def as_dict(self):
         d = {}
@@ -138,6 +140,12 @@ def lib():
         L.tc_profile_read.argtypes = [ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
         L.tc_launch_count.restype = i64
         L.tc_launch_count.argtypes = []
+        L.tc_debug_fail_allocation.restype = i32
+        L.tc_debug_fail_allocation.argtypes = [i64]
+        L.tc_debug_allocations.restype = i64
+        L.tc_debug_allocations.argtypes = []
+        L.tc_debug_live_allocations.restype = i64
+        L.tc_debug_live_allocations.argtypes = []
         L.tc_graph_free.restype = None
         L.tc_graph_free.argtypes = [vp]
         L.tc_status_str.restype = ctypes.c_char_p
@@ -259,7 +267,8 @@ def allreduce_counts(tri, edge_flag, group=None):
     over torch.distributed (NCCL between GPUs, gloo on CPU)."""
     import torch.distributed as dist
     dist.all_reduce(tri.view(torch.int64), op=dist.ReduceOp.SUM, group=group)
-    dist.all_reduce(edge_flag, op=dist.ReduceOp.MAX, group=group)
+    if edge_flag is not None and edge_flag.numel():
+        dist.all_reduce(edge_flag, op=dist.ReduceOp.MAX, group=group)
     return tri, edge_flag
 
 
@@ -385,6 +394,20 @@ def tc_profile_read() -> dict:
 
 def tc_launch_count() -> int:
     return int(lib().tc_launch_count())
+
+
+def tc_debug_fail_allocation(k: int):
+    """Arms one injected device-allocation failure k allocations from now
+    (k < 0 disarms); see include/tc.h."""
+    lib().tc_debug_fail_allocation(int(k))
+
+
+def tc_debug_allocations() -> int:
+    return int(lib().tc_debug_allocations())
+
+
+def tc_debug_live_allocations() -> int:
+    return int(lib().tc_debug_live_allocations())
 
 
 def tc_graph_free(g):

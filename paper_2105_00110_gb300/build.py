@@ -2,15 +2,13 @@
 ``paper_2105_00110_gb300/_build/libtc_gb300.so`` for sm_103a (GB300).
 
 nvcc cross-compiles without a GPU.  Translation units are compiled in
-parallel and linked with the CUDA runtime statically; cuBLAS is linked
-dynamically from the toolkit, whose lib64 the library records as its run
-path.
+parallel and linked with the CUDA runtime statically; the library links
+no other CUDA library (CUB is header-only and compiled in).
 """
 from __future__ import annotations
 
 import json
 import os
-import shutil
 import subprocess
 import sys
 
@@ -33,18 +31,6 @@ def _nvcc() -> str:
         if cand and (os.path.sep not in cand or os.path.exists(cand)):
             return cand
     return "nvcc"
-
-
-def _link_flags() -> list:
-    """cuBLAS (the dense core's matrix product) from the toolkit of nvcc,
-    with that lib64 as the library's run path."""
-    nv = _nvcc()
-    path = nv if os.path.sep in nv else shutil.which(nv)
-    if path:
-        lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(path))), "lib64")
-        if os.path.isdir(lib):
-            return ["-L" + lib, "-Xlinker", "-rpath," + lib, "-lcublas"]
-    return ["-lcublas"]
 
 
 def _stale() -> bool:
@@ -79,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise RuntimeError("nvcc failed for " + ", ".join(failed))
     tmp = LIB + ".tmp%d" % os.getpid()
-    link = [nvcc, *ARCH, "-shared", *objs, *_link_flags(), "-o", tmp]
+    link = [nvcc, *ARCH, "-shared", *objs, "-o", tmp]
     subprocess.check_call(link)
     os.replace(tmp, LIB)
     # the commands this library was made with (read by the build checks)

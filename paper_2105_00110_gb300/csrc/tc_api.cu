@@ -25,6 +25,10 @@ tc_status from_cuda(cudaError_t e) {
 namespace {
 std::once_flag g_pool_once;
 std::atomic<long long> g_launches{0};
+// failure injection and accounting of the device allocations (testing aid)
+std::atomic<long long> g_fail_in{-1};     // allocations left before the injected failure; -1 off
+std::atomic<long long> g_allocs{0};       // device allocations requested since load
+std::atomic<long long> g_live{0};         // device allocations currently held
 
 struct timing_rec {
     const char* name;
@@ -98,17 +102,28 @@ tc_status dalloc(void** p, size_t bytes, cudaStream_t s) {
         }
     });
     *p = nullptr;
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    // an armed injected failure: the allocation that takes the count to -1
+    // fails as a device out-of-memory would, once
+    long long k = g_fail_in.load();
+    while (k >= 0 && !g_fail_in.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 0) return TC_ERR_OUT_OF_MEMORY;
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {
         *p = nullptr;
         return from_cuda(e);
     }
+    g_live.fetch_add(1, std::memory_order_relaxed);
     return TC_OK;
 }
 
 void dfree(void* p, cudaStream_t s) {
-    if (p) cudaFreeAsync(p, s);
+    if (p) {
+        cudaFreeAsync(p, s);
+        g_live.fetch_sub(1, std::memory_order_relaxed);
+    }
 }
 
 void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -176,10 +191,6 @@ void note_launch(const char* name, cudaStream_t s, int phase, bool counts) {
 
 }  // namespace tcx
 
-namespace tcx {
-double core_flop(int64_t C);   // tc_core.cu
-}
-
 using namespace tcx;
 
 extern "C" {
@@ -194,12 +205,14 @@ const char* tc_status_str(tc_status s) {
         case TC_ERR_OVERFLOW: return "3 * triangle count overflows 64 bits";
         case TC_ERR_TIMEOUT: return "device wait timed out";
         case TC_ERR_STATE: return "call order violated";
+        case TC_ERR_BOUNDS: return "a device bounds check failed (bounds-checked build)";
     }
     return "unknown status";
 }
 
 tc_status tc_build_csr(const void* src, const void* dst, int64_t num_pairs, int64_t n,
                        uint32_t flags, tc_stream stream, tc_graph** out) {
+    nvtx_range nr("tc_build_csr");
     if (!out) return TC_ERR_INVALID_ARG;
     *out = nullptr;
     if (num_pairs < 0 || n < 0 || n > INT32_MAX) return TC_ERR_INVALID_ARG;
@@ -226,6 +239,7 @@ tc_status tc_build_csr(const void* src, const void* dst, int64_t num_pairs, int6
 
 tc_status tc_count(tc_graph* g, uint64_t* d_tri, uint8_t* d_edge_flag, uint64_t* h_tri_total,
                    tc_stream stream) {
+    nvtx_range nr("tc_count");
     if (!g) return TC_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     g->stream = s;
@@ -244,6 +258,7 @@ tc_status tc_count(tc_graph* g, uint64_t* d_tri, uint8_t* d_edge_flag, uint64_t*
 
 tc_status tc_edge_triangles(tc_graph* g, uint64_t* d_tri, uint32_t* d_edge_tri, uint64_t* h_tri_total,
                             tc_stream stream) {
+    nvtx_range nr("tc_edge_triangles");
     if (!g) return TC_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     g->stream = s;
@@ -262,6 +277,7 @@ tc_status tc_edge_triangles(tc_graph* g, uint64_t* d_tri, uint32_t* d_edge_tri, 
 
 tc_status tc_count_shard(tc_graph* g, int shard, int num_shards, uint64_t* d_tri, uint8_t* d_edge_flag,
                          uint64_t* h_tri_partial, tc_stream stream) {
+    nvtx_range nr("tc_count_shard");
     if (!g || num_shards < 1 || shard < 0 || shard >= num_shards) return TC_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     g->stream = s;
@@ -278,6 +294,7 @@ tc_status tc_count_shard(tc_graph* g, int shard, int num_shards, uint64_t* d_tri
 
 tc_status tc_load_counts(tc_graph* g, const uint64_t* d_tri, const uint8_t* d_edge_flag, uint64_t* h_tri_total,
                          tc_stream stream) {
+    nvtx_range nr("tc_load_counts");
     if (!g || (g->n > 0 && !d_tri) || (g->m > 0 && !d_edge_flag)) return TC_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     g->stream = s;
@@ -297,6 +314,7 @@ tc_status tc_load_counts(tc_graph* g, const uint64_t* d_tri, const uint8_t* d_ed
 
 tc_status tc_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, uint64_t* h_den,
                         tc_stream stream) {
+    nvtx_range nr("tc_centrality");
     if (!g) return TC_ERR_INVALID_ARG;
     if (!g->counted) return TC_ERR_STATE;
     if (g->total > UINT64_MAX / 3) return TC_ERR_OVERFLOW;
@@ -333,7 +351,6 @@ tc_status tc_get_stats(const tc_graph* g, tc_graph_stats* out) {
     if (!g || !out) return TC_ERR_INVALID_ARG;
     *out = g->stats;
     out->core_vertices = g->core_c;
-    out->core_flop = g->core_c > 0 ? tcx::core_flop(g->core_c) : 0.0;
     return TC_OK;
 }
 
@@ -386,6 +403,15 @@ tc_status tc_profile_read(tc_kernel_time* out, int cap, int* count) {
 }
 
 int64_t tc_launch_count(void) { return (int64_t)g_launches.load(); }
+
+tc_status tc_debug_fail_allocation(int64_t k) {
+    g_fail_in.store(k < 0 ? -1 : (long long)k);
+    return TC_OK;
+}
+
+int64_t tc_debug_allocations(void) { return (int64_t)g_allocs.load(); }
+
+int64_t tc_debug_live_allocations(void) { return (int64_t)g_live.load(); }
 
 void tc_graph_free(tc_graph* g) {
     if (!g) return;

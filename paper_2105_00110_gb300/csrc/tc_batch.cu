@@ -245,6 +245,7 @@ extern "C" {
 tc_status tc_batch_build(const void* src, const void* dst, const int64_t* h_pair_offsets,
                          const int64_t* h_num_vertices, int64_t num_graphs, uint32_t flags,
                          tc_stream stream, tc_batch** out) {
+    tcx::nvtx_range nr("tc_batch_build");
     if (!out) return TC_ERR_INVALID_ARG;
     *out = nullptr;
     if (num_graphs < 0 || (num_graphs > 0 && (!h_pair_offsets || !h_num_vertices)))
@@ -273,6 +274,7 @@ tc_status tc_batch_build(const void* src, const void* dst, const int64_t* h_pair
 
 tc_status tc_batch_run(tc_batch* b, uint64_t* d_tri, uint8_t* d_edge_flag, uint64_t* d_numer, double* d_tc,
                        uint64_t* d_tri_totals, tc_stream stream) {
+    tcx::nvtx_range nr("tc_batch_run");
     if (!b) return TC_ERR_INVALID_ARG;
     return run_batch(b, d_tri, d_edge_flag, d_numer, d_tc, d_tri_totals, (cudaStream_t)stream);
 }

@@ -328,6 +328,16 @@ __device__ __forceinline__ uint32_t visit_octet(const LK& lk, const octet& o, in
 // staged indices of the hits, then the counter atomics — so that the loads
 // of an octet overlap instead of each waiting behind the previous id's
 // atomic.
+#ifndef TC_OCTET_ROTATE
+#define TC_OCTET_ROTATE 1
+#endif
+// Ids of an octet inside its stream: bits [max(0, -off), min(8, len - off)).
+__device__ __forceinline__ uint32_t octet_valid(int off, int len) {
+    const int lo = off < 0 ? -off : 0;
+    const int hi = len - off < 8 ? len - off : 8;
+    return hi > lo ? (0xffu >> (8 - hi)) & (0xffu << lo) : 0u;
+}
+
 template <bool EC>
 __device__ __forceinline__ uint32_t visit_octet_bitmap(const lookup_bitmap& lk, const octet& o, int64_t pos,
                                                        int off, int len, uint32_t* cnt, int64_t h0,
@@ -339,9 +349,18 @@ __device__ __forceinline__ uint32_t visit_octet_bitmap(const lookup_bitmap& lk, 
         word[k] = lk.bits[boff[k] >> 4];
     }
     uint32_t hm = 0;
+    if (TC_OCTET_ROTATE) {
+        // membership bit s = boff & 15 of each entry rotated onto bit k, then
+        // the octet's ids outside the stream masked once
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-        hm |= (((word[k] >> (boff[k] & 15)) & 1u) & ((unsigned)(off + k) < (unsigned)len ? 1u : 0u)) << k;
+        for (int k = 0; k < 8; ++k)
+            hm |= __funnelshift_l(word[k], word[k], (uint32_t)k - (boff[k] & 15u)) & (1u << k);
+        hm &= octet_valid(off, len);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            hm |= (((word[k] >> (boff[k] & 15)) & 1u) & ((unsigned)(off + k) < (unsigned)len ? 1u : 0u)) << k;
+    }
     if (hm == 0) return 0;
     int l[8];
 #pragma unroll
@@ -962,6 +981,7 @@ tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s) {
         st = (x);                \
         if (st < 0) {            \
             cleanup();           \
+            free_plan(p, s);     \
             return st;           \
         }                        \
     } while (0)

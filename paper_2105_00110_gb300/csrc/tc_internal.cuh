@@ -28,6 +28,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <functional>
@@ -101,8 +102,8 @@ struct tc_graph {
     int plan_params_version = 0, params_version = 0;
     tc_graph_stats stats{};
     // dense core: the top core_c ranks, whose mutual triangles the count
-    // takes from one matrix product (0: none; the head entries of a core
-    // row whose lower end is in the core then stream nothing)
+    // takes edge by edge from bit-packed core rows (0: none; the head
+    // entries whose lower end is in the core then stream nothing)
     int64_t core_c = 0;
     // optional per-graph denominators (batches): rank -> graph, Σ△(v) per graph
     const int32_t* rank_graph = nullptr;
@@ -154,10 +155,22 @@ tc_status run_library(const char* site, int64_t size, int64_t bits, bool in_scop
 }
 // phase 0 before, 1 after; counts = false times a copy without counting a launch
 void note_launch(const char* name, cudaStream_t s, int phase, bool counts = true);
+// NVTX range over a host scope (entry points, library phases): shows on a
+// profiler's timeline; without a profiler attached a push/pop costs a few ns.
+struct nvtx_range {
+    explicit nvtx_range(const char* name) { nvtxRangePushA(name); }
+    ~nvtx_range() { nvtxRangePop(); }
+};
 struct launch_scope {
     const char* name; cudaStream_t s;
-    launch_scope(const char* n, cudaStream_t st) : name(n), s(st) { note_launch(name, s, 0); }
-    ~launch_scope() { note_launch(name, s, 1); }
+    launch_scope(const char* n, cudaStream_t st) : name(n), s(st) {
+        nvtxRangePushA(name);
+        note_launch(name, s, 0);
+    }
+    ~launch_scope() {
+        note_launch(name, s, 1);
+        nvtxRangePop();
+    }
 };
 // Times the copies issued inside it under `name` (profile entries named
 // "copy_*"); they are not kernel launches.

@@ -233,6 +233,7 @@ __global__ void k_na_mark(const ull* err, int64_t n, ull* d_tri, ull* d_numer, d
 extern "C" tc_status tc_csr_centrality_noalloc(const int64_t* d_row_ptr, const int32_t* d_col, int64_t n,
                                                int64_t nnz, uint64_t* d_tri, uint64_t* d_numer,
                                                double* d_tc, tc_stream stream) {
+    tcx::nvtx_range nr("tc_csr_centrality_noalloc");
     if (n < 0 || n > kMaxN || nnz < 0 || nnz > kMaxNnz || (nnz & 1)) return TC_ERR_INVALID_ARG;
     if (n == 0 && nnz != 0) return TC_ERR_INVALID_ARG;
     if (n > 0 && !d_row_ptr) return TC_ERR_INVALID_ARG;

@@ -214,7 +214,11 @@ void worker_main(tc_server* srv) {
         }
         const double t_start = srv->now();
         for (request* r : batch) r->info.t_start = t_start;
-        tc_status st = run_requests(batch, stg, s);
+        tc_status st;
+        {
+            tcx::nvtx_range nr("tc_server_batch");
+            st = run_requests(batch, stg, s);
+        }
         if (st < 0 && batch.size() > 1) {
             // one bad request must not fail its batch-mates: rerun each alone
             for (request* r : batch) {

@@ -71,7 +71,8 @@ def test_host_argument_checks_reject_without_device(built):
     # dense-core setting: host only; the build flag that keeps unions of
     # graphs without a core is not a public flag
     assert lib.tc_set_dense_core(-2) == tcg.TC_ERR_INVALID_ARG
-    for c in (0, 4096, -1):
+    assert lib.tc_set_dense_core(32769) == tcg.TC_ERR_INVALID_ARG
+    for c in (0, 4096, 32768, -1):
         assert lib.tc_set_dense_core(c) == tcg.TC_OK
     assert lib.tc_build_csr(None, None, 0, 5, 1 << 30, None, ctypes.byref(h)) == tcg.TC_ERR_INVALID_ARG
 

@@ -1,6 +1,8 @@
-"""The N>1 path of bench.py on CPU: world_size-2 gloo ranks each time their
-own graph; the whole-job time is the slowest rank's and the units add up.
-Ranks draw different graphs (weak scaling over independent graphs)."""
+"""The N>1 paths of bench.py on CPU with world_size-2 gloo ranks: replicas
+(each rank times its own graph; the whole-job time is the slowest rank's
+and the units add up) and the exchange step of one graph sharded across
+the ranks (partial counts summed, flags OR-ed: equal to the unsharded
+oracle result)."""
 from __future__ import annotations
 
 import os
@@ -70,7 +72,6 @@ def _exchange_worker(rank, world, port, q):
 
     import graphgen as gg
     import oracle
-    import paper_2105_00110_gb300 as tcg
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     s, d, n = gg.gnp(40, 0.25, 61)
@@ -90,7 +91,7 @@ def _exchange_worker(rank, world, port, q):
             flags[index[e]] = 1
     t = torch.from_numpy(tri.view(np.int64)).view(torch.uint64)
     f = torch.from_numpy(flags)
-    tcg.allreduce_counts(t, f)
+    bench.shard_exchange(t, f)          # the bench's exchange step of a sharded count
     ok = (np.array_equal(t.view(torch.int64).numpy().view(np.uint64), ref["tri"]) and
           np.array_equal(f.numpy(), ref["flag"][keep]))
     q.put((rank, ok, int(ref["total"])))

@@ -304,3 +304,21 @@ def test_division_large_matches_fraction():
     for a, b in cases:
         assert oracle.div_rn(a, b) == float(Fraction(a, b)), (a, b)
     assert np.isnan(oracle.div_rn(0, 0))
+
+
+@pytest.mark.parametrize("threads", [2, 7])
+@pytest.mark.parametrize("mode", ["definition", "fast"])
+def test_threaded_oracle_equals_single_thread(mode, threads):
+    # the threaded routines time the oracle on all host cores; they must
+    # return exactly what the pinned single-threaded routines return
+    cases = [gg.rmat(12, seed=31), gg.barabasi_albert(3000, 5, seed=32),
+             gg.planted_hierarchy(900, 12, 6, 0.01, seed=33), gg.grid_chung_lu(side=40, seed=34),
+             gg.gnp(60, 0.3, 35), (np.zeros(0, np.int32), np.zeros(0, np.int32), 5),
+             (np.array([0, 1, 1, 3], np.int32), np.array([1, 0, 2, 3], np.int32), 6)]
+    for src, dst, n in cases:
+        a = oracle.run(src, dst, n, mode)
+        b = oracle.run(src, dst, n, mode, threads=threads, algebraic=False)
+        for k in ("ptr", "adj", "t", "flag", "tri", "numer", "core", "noncore"):
+            assert np.array_equal(a[k], b[k]), k
+        assert a["total"] == b["total"] and a["den"] == b["den"]
+        assert np.array_equal(a["tc"].view(np.int64), b["tc"].view(np.int64))
