@@ -351,13 +351,15 @@ def run_ours(args, spec, wl_name):
 
     if rank == 0:
         peak, peak_kind = peaks()
-        # the dominant kernel of the step and its algorithmic bytes per launch
+        # the dominant kernel of the step among those with an algorithmic
+        # byte model (the count classes; the build's scatter-bound kernels
+        # carry none) and its algorithmic bytes per launch
         kern = {k: v for k, v in prof.items()}
-        top = max(kern.items(), key=lambda kv: kv[1][1]) if kern else None
         bytes_per = {name: stats["class_bytes"][c] for name, c in tcg.KERNEL_CLASS.items()}
-        bytes_per["gather"] = stats["centrality_bytes"]
+        modelled = {k: v for k, v in kern.items() if bytes_per.get(k)}
+        top = max(modelled.items(), key=lambda kv: kv[1][1]) if modelled else None
         roof = None
-        if top and top[0] in bytes_per:
+        if top:
             name, (launch_n, tot_ms) = top
             avg_s = tot_ms / launch_n / 1e3
             achieved = bytes_per[name] / avg_s / 1e9

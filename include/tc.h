@@ -311,6 +311,18 @@ tc_status tc_debug_fail_allocation(int64_t k);
 int64_t tc_debug_allocations(void);
 int64_t tc_debug_live_allocations(void);
 
+/*
+ * Bounds-checked builds (compiled with -DTC_DEBUG_BOUNDS; the Python
+ * binding's build(debug=True)): the count, gather and dense-core kernels
+ * check every index they take from graph data against its array and, on a
+ * failure, record it in an error word and skip to a valid entry instead of
+ * faulting; each entry point then synchronises its stream and returns
+ * TC_ERR_BOUNDS.  tc_debug_bounds_build returns 1 in such a build, else 0;
+ * tc_debug_bounds_line the source line of the last failed check (0: none).
+ */
+int tc_debug_bounds_build(void);
+int64_t tc_debug_bounds_line(void);
+
 /* ------------------------------------------------------------------ batches
  * Many independent graphs processed as one: the batch is the disjoint union
  * of its graphs (graph k's vertices shifted by Σ_{j<k} n_j).  Triangles,

@@ -17,7 +17,7 @@ import os
 import numpy as np
 import torch
 
-from .build import LIB, build  # noqa: F401
+from .build import DEBUG_LIB, LIB, build  # noqa: F401
 
 TC_OK = 0
 TC_NO_TRIANGLES = 1
@@ -47,7 +47,8 @@ EXPORTED = ["tc_build_csr", "tc_count", "tc_count_shard", "tc_load_counts", "tc_
             "tc_batch_copy_edges", "tc_batch_get_stats", "tc_batch_autotune", "tc_batch_get_params",
             "tc_batch_free", "tc_csr_centrality_noalloc",
             "tc_server_create", "tc_server_submit", "tc_server_poll", "tc_server_stats", "tc_server_free",
-            "tc_debug_fail_allocation", "tc_debug_allocations", "tc_debug_live_allocations"]
+            "tc_debug_fail_allocation", "tc_debug_allocations", "tc_debug_live_allocations",
+            "tc_debug_bounds_build", "tc_debug_bounds_line"]
 
 
 class TCError(RuntimeError):
@@ -92,15 +93,26 @@ class KernelTime(ctypes.Structure):
 
 
 _lib = None
+_lib_path = LIB
+
+
+def use_library(path: str):
+    """Loads the library from `path` instead of the default build (e.g. the
+    bounds-checked one from build(debug=True)).  Only before the first call
+    into the library."""
+    global _lib_path
+    if _lib is not None and os.path.abspath(path) != os.path.abspath(_lib_path):
+        raise RuntimeError("the library is already loaded from " + _lib_path)
+    _lib_path = path
 
 
 def lib():
     """The loaded library; raises if it has not been built."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB):
+        if not os.path.exists(_lib_path):
             raise RuntimeError("libtc_gb300.so is not built: call paper_2105_00110_gb300.build()")
-        L = ctypes.CDLL(LIB)
+        L = ctypes.CDLL(_lib_path)
         vp, i64, u64, i32, u32 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64,
                                   ctypes.c_int, ctypes.c_uint32)
         L.tc_build_csr.restype = i32
@@ -140,6 +152,10 @@ def lib():
         L.tc_profile_read.argtypes = [ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
         L.tc_launch_count.restype = i64
         L.tc_launch_count.argtypes = []
+        L.tc_debug_bounds_build.restype = i32
+        L.tc_debug_bounds_build.argtypes = []
+        L.tc_debug_bounds_line.restype = i64
+        L.tc_debug_bounds_line.argtypes = []
         L.tc_debug_fail_allocation.restype = i32
         L.tc_debug_fail_allocation.argtypes = [i64]
         L.tc_debug_allocations.restype = i64
@@ -400,6 +416,14 @@ def tc_debug_fail_allocation(k: int):
     """Arms one injected device-allocation failure k allocations from now
     (k < 0 disarms); see include/tc.h."""
     lib().tc_debug_fail_allocation(int(k))
+
+
+def tc_debug_bounds_build() -> bool:
+    return bool(lib().tc_debug_bounds_build())
+
+
+def tc_debug_bounds_line() -> int:
+    return int(lib().tc_debug_bounds_line())
 
 
 def tc_debug_allocations() -> int:

@@ -78,6 +78,36 @@ void drain_locked() {
 }
 }  // namespace
 
+#ifdef TC_DEBUG_BOUNDS
+namespace {
+std::mutex& dbg_mu() {
+    static std::mutex m;
+    return m;
+}
+std::vector<unsigned (*)()>& dbg_readers() {
+    static std::vector<unsigned (*)()> v;
+    return v;
+}
+std::atomic<long long> g_dbg_line{0};
+}  // namespace
+
+void dbg_register(unsigned (*take)()) {
+    std::lock_guard<std::mutex> lk(dbg_mu());
+    dbg_readers().push_back(take);
+}
+
+tc_status dbg_collect() {
+    std::lock_guard<std::mutex> lk(dbg_mu());
+    unsigned line = 0;
+    for (auto take : dbg_readers()) {
+        const unsigned v = take();
+        if (v && !line) line = v;
+    }
+    if (line) g_dbg_line.store(line);
+    return line ? TC_ERR_BOUNDS : TC_OK;
+}
+#endif
+
 int sm_count() {
     static int cached = 0;
     if (!cached) {
@@ -227,6 +257,10 @@ tc_status tc_build_csr(const void* src, const void* dst, int64_t num_pairs, int6
     } catch (...) {
         st = TC_ERR_CUDA;
     }
+    if (st >= 0) st = [&]() -> tc_status {
+        TC_DEBUG_COLLECT((cudaStream_t)stream);   // bounds-checked builds only
+        return TC_OK;
+    }();
     if (st < 0) {
         free_graph_memory(g);
         cudaStreamSynchronize((cudaStream_t)stream);
@@ -250,6 +284,7 @@ tc_status tc_count(tc_graph* g, uint64_t* d_tri, uint8_t* d_edge_flag, uint64_t*
     unsigned long long total = 0;
     TC_CUDA(cudaMemcpyAsync(&total, g->counters, 8, cudaMemcpyDeviceToHost, s));
     TC_CUDA(cudaStreamSynchronize(s));
+    TC_DEBUG_COLLECT(s);
     g->total = total;
     g->counted = 1;
     if (h_tri_total) *h_tri_total = total;
@@ -269,6 +304,7 @@ tc_status tc_edge_triangles(tc_graph* g, uint64_t* d_tri, uint32_t* d_edge_tri, 
     unsigned long long total = 0;
     TC_CUDA(cudaMemcpyAsync(&total, g->counters, 8, cudaMemcpyDeviceToHost, s));
     TC_CUDA(cudaStreamSynchronize(s));
+    TC_DEBUG_COLLECT(s);
     g->total = total;
     g->counted = 1;
     if (h_tri_total) *h_tri_total = total;
@@ -288,6 +324,7 @@ tc_status tc_count_shard(tc_graph* g, int shard, int num_shards, uint64_t* d_tri
     unsigned long long part = 0;
     TC_CUDA(cudaMemcpyAsync(&part, g->counters, 8, cudaMemcpyDeviceToHost, s));
     TC_CUDA(cudaStreamSynchronize(s));
+    TC_DEBUG_COLLECT(s);
     if (h_tri_partial) *h_tri_partial = part;
     return TC_OK;
 }
@@ -303,6 +340,7 @@ tc_status tc_load_counts(tc_graph* g, const uint64_t* d_tri, const uint8_t* d_ed
     unsigned long long sum = 0;
     TC_CUDA(cudaMemcpyAsync(&sum, g->counters, 8, cudaMemcpyDeviceToHost, s));
     TC_CUDA(cudaStreamSynchronize(s));
+    TC_DEBUG_COLLECT(s);
     if (sum % 3 != 0) return TC_ERR_INVALID_ARG;   // Σ △(v) = 3△(G) for any graph
     g->total = sum / 3;
     TC_CUDA(cudaMemcpyAsync(g->counters, &g->total, 8, cudaMemcpyHostToDevice, s));
@@ -320,6 +358,7 @@ tc_status tc_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, uint64_t* 
     if (g->total > UINT64_MAX / 3) return TC_ERR_OVERFLOW;
     g->stream = (cudaStream_t)stream;
     TC_TRY(run_centrality(g, d_numer, d_tc, (cudaStream_t)stream));
+    TC_DEBUG_COLLECT((cudaStream_t)stream);   // bounds-checked builds only: synchronises
     if (h_den) *h_den = 3ull * g->total;
     return g->total == 0 ? TC_NO_TRIANGLES : TC_OK;
 }
@@ -403,6 +442,22 @@ tc_status tc_profile_read(tc_kernel_time* out, int cap, int* count) {
 }
 
 int64_t tc_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int tc_debug_bounds_build(void) {
+#ifdef TC_DEBUG_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int64_t tc_debug_bounds_line(void) {
+#ifdef TC_DEBUG_BOUNDS
+    return (int64_t)tcx::g_dbg_line.load();
+#else
+    return 0;
+#endif
+}
 
 tc_status tc_debug_fail_allocation(int64_t k) {
     g_fail_in.store(k < 0 ? -1 : (long long)k);

@@ -262,6 +262,10 @@ tc_status tc_batch_build(const void* src, const void* dst, const int64_t* h_pair
     } catch (...) {
         st = TC_ERR_OUT_OF_MEMORY;
     }
+    if (st >= 0) st = [&]() -> tc_status {
+        TC_DEBUG_COLLECT(s);   // bounds-checked builds only
+        return TC_OK;
+    }();
     if (st < 0) {
         free_batch(b, s);
         cudaStreamSynchronize(s);
@@ -276,7 +280,9 @@ tc_status tc_batch_run(tc_batch* b, uint64_t* d_tri, uint8_t* d_edge_flag, uint6
                        uint64_t* d_tri_totals, tc_stream stream) {
     tcx::nvtx_range nr("tc_batch_run");
     if (!b) return TC_ERR_INVALID_ARG;
-    return run_batch(b, d_tri, d_edge_flag, d_numer, d_tc, d_tri_totals, (cudaStream_t)stream);
+    TC_TRY(run_batch(b, d_tri, d_edge_flag, d_numer, d_tc, d_tri_totals, (cudaStream_t)stream));
+    TC_DEBUG_COLLECT((cudaStream_t)stream);   // bounds-checked builds only: synchronises
+    return TC_OK;
 }
 
 tc_status tc_batch_info(const tc_batch* b, int64_t* num_graphs, int64_t* num_vertices, int64_t* num_edges,

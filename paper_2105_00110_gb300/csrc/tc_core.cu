@@ -81,7 +81,7 @@ inline size_t pair_smem(int64_t W) {
 // row's own bits, gathered in a per-warp buffer first, also give P.
 __global__ void __launch_bounds__(kFillThreads)
 k_core_fill(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart, const int32_t* __restrict__ col,
-            int64_t t, int64_t C, int64_t W, uint32_t* __restrict__ R, uint16_t* __restrict__ P) {
+            int64_t t, int64_t C, int64_t W, uint32_t* __restrict__ R, uint16_t* __restrict__ P, tc_dims dm) {
     extern __shared__ __align__(16) uint32_t fill_buf[];
     const int lane = threadIdx.x & 31;
     uint32_t* buf = fill_buf + (threadIdx.x >> 5) * W;
@@ -89,14 +89,14 @@ k_core_fill(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hst
     const int K = (int)(W >> 5);   // words per lane for the prefix counts
     for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < C; i += warps) {
         const int64_t r = t + i;
-        const int64_t h = hstart[r], e = row_ptr[r + 1];
+        const int64_t h = hstart[TC_IX(r, dm.n)], e = row_ptr[TC_IX(r, dm.n) + 1];
         for (int w = lane; w < W; w += 32) buf[w] = 0;
         __syncwarp();
         const uint32_t ibit = 1u << (i & 31);
         for (int64_t p = h + lane; p < e; p += 32) {
-            const int64_t j = (int64_t)col[p] - t;   // j > i
-            atomicOr(&buf[j >> 5], 1u << (j & 31));
-            atomicOr(&R[j * W + (i >> 5)], ibit);
+            const int64_t j = (int64_t)col[TC_IX(p, dm.e2)] - t;   // j > i
+            atomicOr(&buf[TC_IX(j >> 5, W)], 1u << (j & 31));
+            atomicOr(&R[TC_IX(j * W + (i >> 5), C * W)], ibit);
         }
         __syncwarp();
         for (int w = lane; w < W; w += 32)
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kPairThreads, 2)
 k_core_pairs(const uint32_t* __restrict__ R, const uint16_t* __restrict__ P, const int64_t* __restrict__ hstart,
              int64_t t, int64_t C, int64_t nvch, int64_t nitems, ull* __restrict__ cursor,
              ull* __restrict__ S, uint32_t* __restrict__ flag, uint32_t* __restrict__ ecnt,
-             ull* __restrict__ sum_t) {
+             ull* __restrict__ sum_t, tc_dims dm) {
     constexpr int W = 128 * KW;
     constexpr int UB = W <= 512 ? 32 : 16;
     extern __shared__ __align__(16) uint8_t pair_dyn[];
@@ -203,7 +203,7 @@ k_core_pairs(const uint32_t* __restrict__ R, const uint16_t* __restrict__ P, con
             for (int k = threadIdx.x; k < UB * W / 8; k += kPairThreads)
                 pdst[k] = k < nrows * W / 8 ? psrc[k] : make_uint4(0, 0, 0, 0);
             if (threadIdx.x < UB) {
-                Hs[threadIdx.x] = threadIdx.x < nrows ? hstart[t + u0 + threadIdx.x] : 0;
+                Hs[threadIdx.x] = threadIdx.x < nrows ? hstart[TC_IX(t + u0 + threadIdx.x, dm.n)] : 0;
                 Su[threadIdx.x] = 0;
             }
         }
@@ -254,13 +254,13 @@ k_core_pairs(const uint32_t* __restrict__ R, const uint16_t* __restrict__ P, con
                         const uint32_t gt = vw > uiw ? 0xffffffffu : ~((2u << (u & 31)) - 1u);
                         const int64_t pos = Hs[b] + Ps[b * W + vw] + __popc(Rs[b * W + vw] & below_v & gt);
                         // fire-and-forget updates: nothing here waits on a global load
-                        if (ecnt) atomicAdd(&ecnt[pos], T);
-                        else atomicOr(&flag[pos >> 5], 1u << (pos & 31));
+                        if (ecnt) atomicAdd(&ecnt[TC_IX(pos, dm.e2)], T);
+                        else atomicOr(&flag[TC_IX(pos >> 5, dm.fw)], 1u << (pos & 31));
                     }
                 }
             }
             if (lane == 0 && vsum) {
-                atomicAdd(&S[v], (ull)vsum);
+                atomicAdd(&S[TC_IX(v, C)], (ull)vsum);
                 all += vsum;
             }
         }
@@ -299,7 +299,7 @@ tc_status launch_pairs(const uint32_t* R, const uint16_t* P, const tc_graph* g, 
     const int blocks = (int)std::min<int64_t>((int64_t)sm_count() * per_sm, nitems);
     launch_scope ls("count_core_pairs", s);
     k_core_pairs<KW><<<blocks, kPairThreads, smem, s>>>(R, P, g->hstart, t, C, nvch, nitems, cursor, S, flag, ecnt,
-                                                       sum_t);
+                                                       sum_t, dims_of(g));
     TC_LAUNCH_CHECK();
     return TC_OK;
 }
@@ -382,7 +382,7 @@ tc_status run_core(tc_graph* g, cudaStream_t s, bool edge_counts) {
                 const size_t smem = (size_t)per * W * 4;
                 if (smem > 48 * 1024)
                     TC_CUDA(cudaFuncSetAttribute(k_core_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                k_core_fill<<<blocks, kFillThreads, smem, s>>>(g->row_ptr, g->hstart, g->col, t, C, W, R, P);
+                k_core_fill<<<blocks, kFillThreads, smem, s>>>(g->row_ptr, g->hstart, g->col, t, C, W, R, P, dims_of(g));
                 TC_LAUNCH_CHECK();
             }
             uint32_t* ec = edge_counts ? g->ecnt : nullptr;

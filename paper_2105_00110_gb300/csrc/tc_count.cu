@@ -84,9 +84,10 @@ struct lookup_bitmap {
     const uint32_t* bits;   // the entries
     int32_t base;
     int32_t nbits;
+    int32_t hv;             // staged ids (counters)
     __device__ __forceinline__ bool find(int32_t w, int& l) const {
         const uint32_t off = min((uint32_t)(w - base), (uint32_t)nbits);
-        const uint32_t e = bits[off >> 4];
+        const uint32_t e = bits[TC_IX(off >> 4, (nbits >> 4) + 1)];
         if (!((e >> (off & 15)) & 1u)) return false;
         l = (int)(e >> 16) + __popc(e & ((1u << (off & 15)) - 1));
         return true;
@@ -150,7 +151,8 @@ __device__ __forceinline__ lookup_bitmap build_bitmap(int t, int nt, uint8_t* re
                                                       int64_t h0, int hv, int32_t nbits,
                                                       const int32_t* __restrict__ col,
                                                       uint32_t*& cnt, Barrier barrier,
-                                                      uint32_t* scan_tmp, int lane, int warp, int nwarps) {
+                                                      uint32_t* scan_tmp, int lane, int warp, int nwarps,
+                                                      const tc_dims& dm) {
     // entry i: membership bits of ids [16 i, 16 i + 16) of the window in its
     // low half, the members before it in its high half
     const int ents = (nbits + 15) >> 4;
@@ -161,8 +163,8 @@ __device__ __forceinline__ lookup_bitmap build_bitmap(int t, int nt, uint8_t* re
     for (int i = t; i < hv; i += nt) cnt[i] = 0;
     barrier();
     for (int i = t; i < hv; i += nt) {
-        const int32_t off = col[h0 + i] - base;
-        atomicOr(&ent[off >> 4], 1u << (off & 15));
+        const int32_t off = col[TC_IX(h0 + i, dm.e2 + 32)] - base;
+        atomicOr(&ent[TC_IX(off >> 4, ents + 1)], 1u << (off & 15));
     }
     barrier();
     const int per = (ents + nt - 1) / nt;
@@ -188,7 +190,7 @@ __device__ __forceinline__ lookup_bitmap build_bitmap(int t, int nt, uint8_t* re
         run += __popc(x);
     }
     barrier();
-    return lookup_bitmap{ent, base, nbits};
+    return lookup_bitmap{ent, base, nbits, hv};
 }
 
 // ------------------------------------------------------------ streams
@@ -215,10 +217,11 @@ struct entry {
     int64_t t;     // twin(u, v)
 };
 
-__device__ __forceinline__ entry fetch_entry(int64_t p, int64_t pe, const tc_head* __restrict__ head) {
+__device__ __forceinline__ entry fetch_entry(int64_t p, int64_t pe, const tc_head* __restrict__ head,
+                                             const tc_dims& dm) {
     entry e{0, 0, 0};
     if (p < pe) {
-        const tc_head rec = head[p];   // one 16-byte load
+        const tc_head rec = head[TC_IX(p, dm.e2)];   // one 16-byte load
         e.r = rec.hrem;
         e.t = rec.twin;
         e.u = rec.u;
@@ -251,33 +254,33 @@ __device__ __forceinline__ void put_stream(const entry& e, int k, int gpre, stre
 // counter per CSR position and a mark adds the number of triangles found
 // on that entry, giving t(u, v) = (A² ∘ A)(u, v) on every canonical entry.
 template <bool EC>
-__device__ __forceinline__ void mark(uint32_t* __restrict__ f, int64_t p, uint32_t c) {
-    if (EC) atomicAdd(&f[p], c);
-    else flag_set(f, p);
+__device__ __forceinline__ void mark(uint32_t* __restrict__ f, int64_t p, uint32_t c, const tc_dims& dm) {
+    if (EC) atomicAdd(&f[TC_IX(p, dm.e2 + 1)], c);
+    else flag_set(f, TC_IX(p, dm.fw * 32));
 }
 // The hits hm (bit k: position pos + k) of one octet (pos 8-aligned).
 template <bool EC>
-__device__ __forceinline__ void mark_octet(uint32_t* __restrict__ f, int64_t pos, uint32_t hm) {
+__device__ __forceinline__ void mark_octet(uint32_t* __restrict__ f, int64_t pos, uint32_t hm, const tc_dims& dm) {
     if (EC) {
         while (hm) {
             const int k = __ffs(hm) - 1;
             hm &= hm - 1;
-            atomicAdd(&f[pos + k], 1u);
+            atomicAdd(&f[TC_IX(pos + k, dm.e2 + 1)], 1u);
         }
     } else if (hm) {
         // the octet's 8 flag bits lie in one 32-bit word
-        flag_or(f, pos >> 5, hm << (pos & 31));
+        flag_or(f, TC_IX(pos >> 5, dm.fw), hm << (pos & 31));
     }
 }
 
 // Credits the hits of stream k to △(u) and flags the edge (u, v).
 template <int N, bool EC>
 __device__ __forceinline__ void close_stream(int k, stream_table<N>& tb, ull* __restrict__ tri,
-                                             uint32_t* __restrict__ flag, ull& tv) {
+                                             uint32_t* __restrict__ flag, ull& tv, const tc_dims& dm) {
     const uint32_t c = tb.hits[k];
     if (c) {
-        atomicAdd(&tri[tb.u[k]], (ull)c);
-        mark<EC>(flag, tb.va[k] + (tb.fl[k] & 7) - 1, c);   // twin(u, v): the canonical entry of (u, v)
+        atomicAdd(&tri[TC_IX(tb.u[k], dm.n)], (ull)c);
+        mark<EC>(flag, tb.va[k] + (tb.fl[k] & 7) - 1, c, dm);   // twin(u, v): the canonical entry of (u, v)
         tv += c;
     }
 }
@@ -303,7 +306,7 @@ __device__ __forceinline__ octet load8(const int32_t* __restrict__ col, int64_t 
 template <class LK, bool CNT, bool EC>
 __device__ __forceinline__ uint32_t visit_octet(const LK& lk, const octet& o, int64_t pos, int off, int len,
                                                 uint32_t* cnt, int64_t h0, ull* __restrict__ tri,
-                                                uint32_t* __restrict__ flag) {
+                                                uint32_t* __restrict__ flag, const tc_dims& dm) {
     uint32_t bits = 0;
     uint32_t nh = 0;
 #pragma unroll
@@ -311,16 +314,16 @@ __device__ __forceinline__ uint32_t visit_octet(const LK& lk, const octet& o, in
         int l = 0;
         if ((unsigned)(off + k) < (unsigned)len && lk.find(o.x[k], l)) {
             if (CNT) {
-                atomicAdd(&cnt[l], 1u);
+                atomicAdd(&cnt[TC_IX(l, lk.hv)], 1u);
             } else {
-                atomicAdd(&tri[o.x[k]], 1ull);
-                mark<EC>(flag, h0 + l, 1u);
+                atomicAdd(&tri[TC_IX(o.x[k], dm.n)], 1ull);
+                mark<EC>(flag, h0 + l, 1u, dm);
             }
             bits |= 1u << k;
             ++nh;
         }
     }
-    mark_octet<EC>(flag, pos, bits);
+    mark_octet<EC>(flag, pos, bits, dm);
     return nh;
 }
 
@@ -341,12 +344,13 @@ __device__ __forceinline__ uint32_t octet_valid(int off, int len) {
 template <bool EC>
 __device__ __forceinline__ uint32_t visit_octet_bitmap(const lookup_bitmap& lk, const octet& o, int64_t pos,
                                                        int off, int len, uint32_t* cnt, int64_t h0,
-                                                       ull* __restrict__ tri, uint32_t* __restrict__ flag) {
+                                                       ull* __restrict__ tri, uint32_t* __restrict__ flag,
+                                                       const tc_dims& dm) {
     uint32_t word[8], boff[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         boff[k] = min((uint32_t)(o.x[k] - lk.base), (uint32_t)lk.nbits);
-        word[k] = lk.bits[boff[k] >> 4];
+        word[k] = lk.bits[TC_IX(boff[k] >> 4, (lk.nbits >> 4) + 1)];
     }
     uint32_t hm = 0;
     if (TC_OCTET_ROTATE) {
@@ -368,8 +372,8 @@ __device__ __forceinline__ uint32_t visit_octet_bitmap(const lookup_bitmap& lk, 
         l[k] = (hm >> k) & 1u ? (int)(word[k] >> 16) + __popc(word[k] & ((1u << (boff[k] & 15)) - 1)) : 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-        if ((hm >> k) & 1u) atomicAdd(&cnt[l[k]], 1u);
-    mark_octet<EC>(flag, pos, hm);
+        if ((hm >> k) & 1u) atomicAdd(&cnt[TC_IX(l[k], lk.hv)], 1u);
+    mark_octet<EC>(flag, pos, hm, dm);
     return (uint32_t)__popc(hm);
 }
 
@@ -382,7 +386,7 @@ template <class LK, bool CNT, int N, int G, bool EC>
 __device__ __forceinline__ void walk_groups(int lane, stream_table<N>& tb, int nc, int gb, int ge,
                                             const LK& lk, uint32_t* cnt, int64_t h0,
                                             const int32_t* __restrict__ col, ull* __restrict__ tri,
-                                            uint32_t* __restrict__ flag) {
+                                            uint32_t* __restrict__ flag, const tc_dims& dm) {
     if (gb >= ge) return;
     int s_base = -1;
     if (gb > 0) {   // last stream starting at or before group gb - 1
@@ -408,13 +412,13 @@ __device__ __forceinline__ void walk_groups(int lane, stream_table<N>& tb, int n
             const int off0 = 8 * G * go - (f & 7), len = f >> 3;
             octet o[G];
 #pragma unroll
-            for (int j = 0; j < G; ++j) o[j] = load8(col, pos + 8 * j);
+            for (int j = 0; j < G; ++j) o[j] = load8(col, TC_IX(pos + 8 * j, dm.e2 + 25));
 #pragma unroll
             for (int j = 0; j < G; ++j)
                 if constexpr (std::is_same<LK, lookup_bitmap>::value && CNT)
-                    h += visit_octet_bitmap<EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, h0, tri, flag);
+                    h += visit_octet_bitmap<EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, h0, tri, flag, dm);
                 else
-                    h += visit_octet<LK, CNT, EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, h0, tri, flag);
+                    h += visit_octet<LK, CNT, EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, h0, tri, flag, dm);
         }
         if ((smask & ~1u) == 0) {
             // the whole window lies in one stream
@@ -435,11 +439,11 @@ template <int N, bool EC>
 __device__ __forceinline__ void merge_streams(int lane, int k0, int k1, stream_table<N>& tb,
                                               const int32_t* A, int na, uint32_t* cnt,
                                               const int32_t* __restrict__ col,
-                                              uint32_t* __restrict__ flag) {
+                                              uint32_t* __restrict__ flag, const tc_dims& dm) {
     for (int i = k0; i < k1; ++i) {
         const int nb = tb.fl[i] >> 3;
         const int64_t p0 = tb.va[i] + (tb.fl[i] & 7);
-        const int32_t* B = col + p0;
+        const int32_t* B = col + TC_IX(p0, dm.e2 + 32);
         const int L = na + nb;
         const int d0 = (int)(((int64_t)L * lane) >> 5), d1 = (int)(((int64_t)L * (lane + 1)) >> 5);
         int lo = max(0, d0 - nb), hi = min(d0, na);
@@ -452,8 +456,8 @@ __device__ __forceinline__ void merge_streams(int lane, int k0, int k1, stream_t
         for (int d = d0; d < d1; ++d) {
             if (ia < na && (jb >= nb || A[ia] <= __ldg(B + jb))) {
                 if (jb < nb && __ldg(B + jb) == A[ia]) {
-                    atomicAdd(&cnt[ia], 1u);
-                    mark<EC>(flag, p0 + jb, 1u);
+                    atomicAdd(&cnt[TC_IX(ia, na)], 1u);
+                    mark<EC>(flag, p0 + jb, 1u, dm);
                     ++found;
                 }
                 ++ia;
@@ -518,7 +522,7 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
              const int32_t* __restrict__ it_v,
              const int64_t* __restrict__ it_pb, const int64_t* __restrict__ it_pe,
              int64_t n_items, int64_t it_off, int64_t it_stride, ull* __restrict__ cursor, int strategy,
-             ull* __restrict__ tri, uint32_t* __restrict__ flag, ull* __restrict__ total) {
+             ull* __restrict__ tri, uint32_t* __restrict__ flag, ull* __restrict__ total, tc_dims dm) {
     __shared__ __align__(16) warp_smem sm[kCtaWarps];
     const int lane = threadIdx.x & 31;
     warp_smem& ws = sm[threadIdx.x >> 5];
@@ -535,21 +539,21 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
             const int64_t gi = it_off + it_stride * it;   // this shard's it-th item
             const int32_t v = it_v[gi];
             const int64_t pb = it_pb[gi], pe = it_pe[gi];
-            entry nxt = fetch_entry(pb + lane, pe, head);
-            const int64_t h0 = hstart[v], h1 = row_ptr[v + 1];
+            entry nxt = fetch_entry(pb + lane, pe, head, dm);
+            const int64_t h0 = hstart[TC_IX(v, dm.n)], h1 = row_ptr[TC_IX(v, dm.n) + 1];
             const int hv = (int)(h1 - h0);
-            const int32_t nbits = col[h1 - 1] - v;
+            const int32_t nbits = col[TC_IX(h1 - 1, dm.e2)] - v;
             const bool use_bitmap = allow_bitmap && warp_bitmap_fits((nbits + 31) >> 5, hv);
             uint32_t* cnt;
             lookup_bitmap lb{};
             int32_t* ids = (int32_t*)ws.region;
             if (use_bitmap) {
-                lb = build_bitmap(lane, 32, ws.region, v, h0, hv, nbits, col, cnt, wbar, nullptr, lane, 0, 1);
+                lb = build_bitmap(lane, 32, ws.region, v, h0, hv, nbits, col, cnt, wbar, nullptr, lane, 0, 1, dm);
             } else {
                 cnt = (uint32_t*)(ids + TC_WARP_CAP);
                 for (int i = lane; i < hv; i += 32) {
-                    ids[i] = col[h0 + i];
-                    cnt[i] = 0;
+                    ids[TC_IX(i, TC_WARP_CAP)] = col[TC_IX(h0 + i, dm.e2)];
+                    cnt[TC_IX(i, TC_WARP_CAP)] = 0;
                 }
                 __syncwarp();
             }
@@ -557,25 +561,25 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
             ull tv = 0;
             for (int64_t b = pb; b < pe; b += 32) {
                 const entry cur = nxt;
-                nxt = fetch_entry(b + 32 + lane, pe, head);   // in flight meanwhile
+                nxt = fetch_entry(b + 32 + lane, pe, head, dm);   // in flight meanwhile
                 int nc;
                 const int groups = compact_warp<kWarpG>(lane, cur, ws.tb, nc);
-                if (MERGE) merge_streams<32, EC>(lane, 0, nc, ws.tb, ids, hv, cnt, col, flag);
-                else if (use_bitmap) walk_groups<lookup_bitmap, true, 32, kWarpG, EC>(lane, ws.tb, nc, 0, groups, lb, cnt, h0, col, tri, flag);
-                else walk_groups<lookup_sorted, true, 32, kWarpG, EC>(lane, ws.tb, nc, 0, groups, ls, cnt, h0, col, tri, flag);
+                if (MERGE) merge_streams<32, EC>(lane, 0, nc, ws.tb, ids, hv, cnt, col, flag, dm);
+                else if (use_bitmap) walk_groups<lookup_bitmap, true, 32, kWarpG, EC>(lane, ws.tb, nc, 0, groups, lb, cnt, h0, col, tri, flag, dm);
+                else walk_groups<lookup_sorted, true, 32, kWarpG, EC>(lane, ws.tb, nc, 0, groups, ls, cnt, h0, col, tri, flag, dm);
                 __syncwarp();
-                if (lane < nc) close_stream<32, EC>(lane, ws.tb, tri, flag, tv);
+                if (lane < nc) close_stream<32, EC>(lane, ws.tb, tri, flag, tv, dm);
                 __syncwarp();
             }
             for (int i = lane; i < hv; i += 32) {
                 const uint32_t c = cnt[i];
                 if (c) {
-                    atomicAdd(&tri[col[h0 + i]], (ull)c);
-                    mark<EC>(flag, h0 + i, c);
+                    atomicAdd(&tri[TC_IX(col[TC_IX(h0 + i, dm.e2)], dm.n)], (ull)c);
+                    mark<EC>(flag, h0 + i, c, dm);
                 }
             }
             tv = warp_sum(tv);
-            if (lane == 0 && tv) atomicAdd(&tri[v], tv);
+            if (lane == 0 && tv) atomicAdd(&tri[TC_IX(v, dm.n)], tv);
             tv_all += tv;
             __syncwarp();
         }
@@ -596,7 +600,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             const int64_t* __restrict__ it_pb, const int64_t* __restrict__ it_pe,
             int64_t n_items, int64_t it_off, int64_t it_stride, ull* __restrict__ cursor, int strategy,
             ull* __restrict__ tri,
-            uint32_t* __restrict__ flag, ull* __restrict__ total) {
+            uint32_t* __restrict__ flag, ull* __restrict__ total, tc_dims dm) {
     extern __shared__ __align__(16) uint8_t dyn[];
     __shared__ __align__(16) stream_table<kCtaT> tb;
     __shared__ int64_t s_item;
@@ -615,20 +619,21 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         const int64_t gi = it_off + it_stride * it;   // this shard's it-th item
         const int32_t v = it_v[gi];
         const int64_t pb = it_pb[gi], pe = it_pe[gi];
-        entry nxt = fetch_entry(pb + t, pe, head);
-        const int64_t h0 = hstart[v], h1 = row_ptr[v + 1];
+        entry nxt = fetch_entry(pb + t, pe, head, dm);
+        const int64_t h0 = hstart[TC_IX(v, dm.n)], h1 = row_ptr[TC_IX(v, dm.n) + 1];
         const int hv = (int)(h1 - h0);
         uint32_t* cnt = nullptr;
         lookup_bitmap lb{};
         lookup_sorted ls{};
         lookup_global lg{};
         if (LOOK == L_BITMAP) {
-            lb = build_bitmap(t, nt, dyn, v, h0, hv, col[h1 - 1] - v, col, cnt, cbar, s_scan, lane, warp, kCtaItemWarps);
+            lb = build_bitmap(t, nt, dyn, v, h0, hv, col[TC_IX(h1 - 1, dm.e2)] - v, col, cnt, cbar, s_scan, lane, warp,
+                              kCtaItemWarps, dm);
         } else if (LOOK == L_SORTED) {
             int32_t* ids = (int32_t*)dyn;
             cnt = (uint32_t*)(ids + hv);
             for (int i = t; i < hv; i += nt) {
-                ids[i] = col[h0 + i];
+                ids[i] = col[TC_IX(h0 + i, dm.e2)];
                 cnt[i] = 0;
             }
             __syncthreads();
@@ -639,7 +644,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         ull tv = 0;
         for (int64_t r0 = pb; r0 < pe; r0 += kCtaT) {
             const entry cur = nxt;
-            nxt = fetch_entry(r0 + kCtaT + t, pe, head);   // in flight meanwhile
+            nxt = fetch_entry(r0 + kCtaT + t, pe, head, dm);   // in flight meanwhile
             // compact the round's non-empty streams: warp scans of the group
             // counts, then the warp totals
             const int ng = entry_groups<kCtaG>(cur);
@@ -667,21 +672,21 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             if (ng > 0) put_stream(cur, before_c + __popc(nz & ((1u << lane) - 1)), before_g + incl - ng, tb);
             __syncthreads();
             if (MERGE) {
-                merge_streams<kCtaT, EC>(lane, (NC * warp) / kCtaItemWarps, (NC * (warp + 1)) / kCtaItemWarps, tb, ls.ids, hv, cnt, col, flag);
+                merge_streams<kCtaT, EC>(lane, (NC * warp) / kCtaItemWarps, (NC * (warp + 1)) / kCtaItemWarps, tb, ls.ids, hv, cnt, col, flag, dm);
             } else {
                 const int gb = (int)(((int64_t)GT * warp) / kCtaItemWarps), ge = (int)(((int64_t)GT * (warp + 1)) / kCtaItemWarps);
                 if (LOOK == L_BITMAP)
-                    walk_groups<lookup_bitmap, true, kCtaT, kCtaG, EC>(lane, tb, NC, gb, ge, lb, cnt, h0, col, tri, flag);
+                    walk_groups<lookup_bitmap, true, kCtaT, kCtaG, EC>(lane, tb, NC, gb, ge, lb, cnt, h0, col, tri, flag, dm);
                 else if (LOOK == L_SORTED)
-                    walk_groups<lookup_sorted, true, kCtaT, kCtaG, EC>(lane, tb, NC, gb, ge, ls, cnt, h0, col, tri, flag);
+                    walk_groups<lookup_sorted, true, kCtaT, kCtaG, EC>(lane, tb, NC, gb, ge, ls, cnt, h0, col, tri, flag, dm);
                 else
-                    walk_groups<lookup_global, false, kCtaT, kCtaG, EC>(lane, tb, NC, gb, ge, lg, nullptr, h0, col, tri, flag);
+                    walk_groups<lookup_global, false, kCtaT, kCtaG, EC>(lane, tb, NC, gb, ge, lg, nullptr, h0, col, tri, flag, dm);
             }
             __syncthreads();   // every group of the round is done
             // no barrier after the closes: the next round rewrites the table
             // only after its first barrier, which every thread reaches once
             // its own close is done
-            if (t < NC) close_stream<kCtaT, EC>(t, tb, tri, flag, tv);
+            if (t < NC) close_stream<kCtaT, EC>(t, tb, tri, flag, tv, dm);
         }
         tv = warp_sum(tv);
         if (lane == 0) s_tv[warp] = tv;
@@ -690,8 +695,8 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             for (int i = t; i < hv; i += nt) {
                 const uint32_t c = cnt[i];
                 if (c) {
-                    atomicAdd(&tri[col[h0 + i]], (ull)c);
-                    mark<EC>(flag, h0 + i, c);
+                    atomicAdd(&tri[TC_IX(col[TC_IX(h0 + i, dm.e2)], dm.n)], (ull)c);
+                    mark<EC>(flag, h0 + i, c, dm);
                 }
             }
         }
@@ -699,7 +704,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             ull sum = 0;
             for (int k = 0; k < kCtaItemWarps; ++k) sum += s_tv[k];
             if (sum) {
-                atomicAdd(&tri[v], sum);
+                atomicAdd(&tri[TC_IX(v, dm.n)], sum);
                 atomicAdd(total, sum);
             }
         }
@@ -717,52 +722,74 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
 #ifndef TC_THREAD_MAX_WORK
 #define TC_THREAD_MAX_WORK 64
 #endif
-constexpr int kThreadMaxH = 32;
+#ifndef TC_THREAD_MAX_H
+#define TC_THREAD_MAX_H 32
+#endif
+#ifndef TC_THREAD_BLOCK
+#define TC_THREAD_BLOCK 256
+#endif
+constexpr int kThreadMaxH = TC_THREAD_MAX_H;      // staged ids per thread (a column of S)
 constexpr int64_t kThreadMaxWork = TC_THREAD_MAX_WORK;
+constexpr int kThreadBlock = TC_THREAD_BLOCK;     // threads of the thread-item kernel
+static_assert(kThreadMaxH * kThreadBlock * 4 <= 48 * 1024, "thread-item staging exceeds static shared memory");
 
 template <bool EC>
-__global__ void __launch_bounds__(TC_CTA_THREADS)
+__global__ void __launch_bounds__(kThreadBlock)
 k_count_thread(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
                const int32_t* __restrict__ it_v, const int64_t* __restrict__ it_pb,
                const int64_t* __restrict__ it_pe, int64_t n_items, int64_t it_off, int64_t it_stride,
                ull* __restrict__ cursor, int strategy,
-               ull* __restrict__ tri, uint32_t* __restrict__ flag, ull* __restrict__ total) {
-    __shared__ int32_t S[kThreadMaxH][TC_CTA_THREADS];
+               ull* __restrict__ tri, uint32_t* __restrict__ flag, ull* __restrict__ total, tc_dims dm) {
+    __shared__ int32_t S[kThreadMaxH][kThreadBlock];
     const int t = threadIdx.x;
     ull tv_all = 0;
     for (int64_t it = blockIdx.x * (int64_t)blockDim.x + t; it < n_items; it += (int64_t)gridDim.x * blockDim.x) {
         const int64_t gi = it_off + it_stride * it;   // this shard's it-th item
         const int32_t v = it_v[gi];
-        const int64_t h0 = hstart[v], h1 = row_ptr[v + 1];
+        const int64_t h0 = hstart[TC_IX(v, dm.n)], h1 = row_ptr[TC_IX(v, dm.n) + 1];
         const int hv = (int)(h1 - h0);
-        for (int k = 0; k < hv; ++k) S[k][t] = col[h0 + k];
+        for (int k = 0; k < hv; ++k) S[TC_IX(k, kThreadMaxH)][t] = col[TC_IX(h0 + k, dm.e2)];
         ull tv = 0;
         const int64_t pe = it_pe[gi];
         for (int64_t p = it_pb[gi]; p < pe; ++p) {
-            const tc_head rec = head[p];
+            const tc_head rec = head[TC_IX(p, dm.e2)];
             const int64_t q0 = rec.twin + 1;
             const int len = rec.hrem;
             uint32_t hits = 0;
+            // first staged id not below the stream's first id (bisection)
             int a = 0;
+            if (len > 0) {
+                const int32_t w0 = col[TC_IX(q0, dm.e2)];
+                int cnt = hv;
+                while (cnt > 0) {
+                    const int half = cnt >> 1;
+                    if (S[a + half][t] < w0) {
+                        a += half + 1;
+                        cnt -= half + 1;
+                    } else {
+                        cnt = half;
+                    }
+                }
+            }
             for (int j = 0; j < len && a < hv; ++j) {
-                const int32_t w = col[q0 + j];
+                const int32_t w = col[TC_IX(q0 + j, dm.e2)];
                 while (a < hv && S[a][t] < w) ++a;
                 if (a < hv && S[a][t] == w) {
-                    atomicAdd(&tri[w], 1ull);
-                    mark<EC>(flag, q0 + j, 1u);
-                    mark<EC>(flag, h0 + a, 1u);
+                    atomicAdd(&tri[TC_IX(w, dm.n)], 1ull);
+                    mark<EC>(flag, q0 + j, 1u, dm);
+                    mark<EC>(flag, h0 + a, 1u, dm);
                     ++hits;
                     ++a;
                 }
             }
             if (hits) {
-                atomicAdd(&tri[rec.u], (ull)hits);
-                mark<EC>(flag, rec.twin, hits);
+                atomicAdd(&tri[TC_IX(rec.u, dm.n)], (ull)hits);
+                mark<EC>(flag, rec.twin, hits, dm);
                 tv += hits;
             }
         }
-        if (tv) atomicAdd(&tri[v], tv);
+        if (tv) atomicAdd(&tri[TC_IX(v, dm.n)], tv);
         tv_all += tv;
     }
     tv_all = warp_sum(tv_all);
@@ -939,7 +966,7 @@ tc_status launch_persistent(K kernel, const char* name, size_t smem, int64_t all
     kernel<<<(int)blocks, threads, smem, s>>>(g->row_ptr, g->col, g->hstart, g->head,
                                                      p.v[c], p.pb[c], p.pe[c], items, (int64_t)shard,
                                                      (int64_t)num_shards, cursor,
-                                                     g->strategy, g->tri, marks, g->counters);
+                                                     g->strategy, g->tri, marks, g->counters, dims_of(g));
     TC_LAUNCH_CHECK();
     return TC_OK;
 }
@@ -1075,7 +1102,7 @@ tc_status launch_count_kernels(tc_graph* g, cudaStream_t s, uint32_t* marks, int
                          EC ? "count_edges_warp" : "count_warp"};
     TC_TRY(launch_persistent(k_count_thread<EC>, EC ? "count_edges_thread" : "count_thread", 0,
                              p.count[TC_CLS_THREAD], s, g, p, TC_CLS_THREAD, cur + TC_CLS_THREAD, marks, shard,
-                             num_shards));
+                             num_shards, kThreadBlock));
     // heaviest classes first; each kernel drains its own item queue
     TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC>, nm[0], p.smem[TC_CLS_BITMAP_L],
                              p.count[TC_CLS_BITMAP_L], s, g, p, TC_CLS_BITMAP_L, cur + TC_CLS_BITMAP_L, marks,

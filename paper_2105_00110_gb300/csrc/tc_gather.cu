@@ -88,11 +88,23 @@ struct gather_args {
     ull* numer_rank;
     ull* numer_out;
     double* tc_out;
+    tc_dims dm;
 };
+
+// One adjacency entry's term (flag ? 1 : 3)·△(u): a head entry's record
+// gives u and the twin position holding its flag, a tail entry holds u in
+// col and its flag in place.
+__device__ __forceinline__ ull head_term(const gather_args& a, int64_t p) {
+    const tc_head rec = a.head[TC_IX(p, a.dm.e2)];
+    return (flag_get(a.flag, TC_IX(rec.twin, a.dm.fw * 32)) ? 1ull : 3ull) * a.tri[TC_IX(rec.u, a.dm.n)];
+}
+__device__ __forceinline__ ull tail_term(const gather_args& a, int64_t p) {
+    return (flag_get(a.flag, TC_IX(p, a.dm.fw * 32)) ? 1ull : 3ull) * a.tri[TC_IX(a.col[TC_IX(p, a.dm.e2)], a.dm.n)];
+}
 
 __device__ __forceinline__ void finish_row(int64_t r, ull acc, const gather_args& a) {
     a.numer_rank[r] = acc;
-    const int32_t v = a.perm[r];
+    const int32_t v = a.perm[TC_IX(r, a.dm.n)];
     if (a.numer_out) a.numer_out[v] = acc;
     if (a.tc_out) a.tc_out[v] = div_rn(acc, a.rank_graph ? a.den_graph[a.rank_graph[r]] : a.den);
 }
@@ -103,11 +115,8 @@ __global__ void __launch_bounds__(256) k_gather_thread(gather_args a, int64_t r0
          r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = a.row_ptr[r], h = a.hstart[r], e = a.row_ptr[r + 1];
         ull acc = a.tri[r];
-        for (int64_t p = b; p < h; ++p) {
-            const tc_head rec = a.head[p];
-            acc += (flag_get(a.flag, rec.twin) ? 1ull : 3ull) * a.tri[rec.u];
-        }
-        for (int64_t p = h; p < e; ++p) acc += (flag_get(a.flag, p) ? 1ull : 3ull) * a.tri[a.col[p]];
+        for (int64_t p = b; p < h; ++p) acc += head_term(a, p);
+        for (int64_t p = h; p < e; ++p) acc += tail_term(a, p);
         finish_row(r, acc, a);
     }
 }
@@ -119,11 +128,8 @@ __global__ void __launch_bounds__(256) k_gather_warp(gather_args a, int64_t r0, 
     for (int64_t r = r0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); r < r1; r += warps) {
         const int64_t b = a.row_ptr[r], h = a.hstart[r], e = a.row_ptr[r + 1];
         ull acc = 0;
-        for (int64_t p = b + lane; p < h; p += 32) {
-            const tc_head rec = a.head[p];
-            acc += (flag_get(a.flag, rec.twin) ? 1ull : 3ull) * a.tri[rec.u];
-        }
-        for (int64_t p = h + lane; p < e; p += 32) acc += (flag_get(a.flag, p) ? 1ull : 3ull) * a.tri[a.col[p]];
+        for (int64_t p = b + lane; p < h; p += 32) acc += head_term(a, p);
+        for (int64_t p = h + lane; p < e; p += 32) acc += tail_term(a, p);
         acc = warp_sum(acc);
         if (lane == 0) finish_row(r, acc + a.tri[r], a);
     }
@@ -136,11 +142,8 @@ __global__ void __launch_bounds__(1024) k_gather_cta(gather_args a, int64_t r0, 
     for (int64_t r = r0 + blockIdx.x; r < r1; r += gridDim.x) {
         const int64_t b = a.row_ptr[r], h = a.hstart[r], e = a.row_ptr[r + 1];
         ull acc = 0;
-        for (int64_t p = b + threadIdx.x; p < h; p += blockDim.x) {
-            const tc_head rec = a.head[p];
-            acc += (flag_get(a.flag, rec.twin) ? 1ull : 3ull) * a.tri[rec.u];
-        }
-        for (int64_t p = h + threadIdx.x; p < e; p += blockDim.x) acc += (flag_get(a.flag, p) ? 1ull : 3ull) * a.tri[a.col[p]];
+        for (int64_t p = b + threadIdx.x; p < h; p += blockDim.x) acc += head_term(a, p);
+        for (int64_t p = h + threadIdx.x; p < e; p += blockDim.x) acc += tail_term(a, p);
         acc = warp_sum(acc);
         if (lane == 0) part[warp] = acc;
         __syncthreads();
@@ -231,7 +234,8 @@ tc_status run_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, cudaStrea
     const int64_t n = g->n;
     if (n == 0) return TC_OK;
     gather_args a{g->row_ptr, g->hstart, g->col, g->head, g->flag, g->tri, g->perm,
-                  3ull * (ull)g->total, g->rank_graph, g->den_graph, g->numer, (ull*)d_numer, d_tc};
+                  3ull * (ull)g->total, g->rank_graph, g->den_graph, g->numer, (ull*)d_numer, d_tc,
+                  dims_of(g)};
     const int64_t r1 = g->band[0], r2 = g->band[1];   // degree <= 32 | <= 4096 | larger
     if (r1 > 0) {
         launch_scope ls("gather_thread", s);

@@ -110,6 +110,71 @@ struct tc_graph {
     const unsigned long long* den_graph = nullptr;
 };
 
+#define TC_TRY(expr)                                    \
+    do {                                                \
+        tc_status _st = (expr);                         \
+        if (_st < 0) return _st;                        \
+    } while (0)
+
+#define TC_CUDA(expr)                                   \
+    do {                                                \
+        cudaError_t _e = (expr);                        \
+        if (_e != cudaSuccess) return tcx::from_cuda(_e); \
+    } while (0)
+
+#define TC_LAUNCH_CHECK() TC_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------- bounds checks
+// Sizes of a built graph's arrays, handed to the kernels whose indices
+// come from graph data, for the bounds-checked build.
+struct tc_dims {
+    int64_t n;    // vertices: tri, numer, perm, hstart (rank space)
+    int64_t e2;   // CSR entries (2m): head, ecnt; col holds e2 + 32 (guard ids)
+    int64_t fw;   // 32-bit words of the flag bitmap
+};
+
+// Bounds-checked builds (-DTC_DEBUG_BOUNDS): TC_IX(i, size) checks an
+// index against its array's size.  A failed check records its source line
+// in this translation unit's error word and redirects the access to entry
+// 0 (every checked array has one), so the kernel never leaves its buffers;
+// the entry point then returns TC_ERR_BOUNDS.  No trap, no device assert.
+// In other builds TC_IX(i, size) is just i.
+#ifdef TC_DEBUG_BOUNDS
+static __device__ unsigned int tc_dbg_err_word;
+template <class I>
+__device__ __forceinline__ I tc_dbg_ix(I i, long long size, int line) {
+    if ((unsigned long long)(long long)i >= (unsigned long long)size) {
+        atomicCAS(&tc_dbg_err_word, 0u, (unsigned)line);
+        return (I)0;
+    }
+    return i;
+}
+#define TC_IX(i, size) tc_dbg_ix((i), (long long)(size), __LINE__)
+namespace tcx {
+// every translation unit registers a reader of its own error word
+void dbg_register(unsigned (*take)());
+// reads and clears every unit's word: TC_ERR_BOUNDS if one was set
+tc_status dbg_collect();
+static unsigned dbg_take_here() {
+    unsigned v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, tc_dbg_err_word, sizeof(v)) != cudaSuccess) return 0;
+    if (v) cudaMemcpyToSymbol(tc_dbg_err_word, &z, sizeof(z));
+    return v;
+}
+static const bool tc_dbg_registered = (dbg_register(&dbg_take_here), true);
+}  // namespace tcx
+#define TC_DEBUG_COLLECT(s)                                   \
+    do {                                                      \
+        TC_CUDA(cudaStreamSynchronize(s));                    \
+        TC_TRY(tcx::dbg_collect());                           \
+    } while (0)
+#else
+#define TC_IX(i, size) (i)
+#define TC_DEBUG_COLLECT(s) \
+    do {                    \
+    } while (0)
+#endif
+
 // ---------------------------------------------------------------- helpers
 // Edge flags, one bit per CSR position.  Bits only ever turn on, so a read
 // that may be stale can only under-report set bits: an OR is issued only
@@ -125,6 +190,7 @@ __device__ __forceinline__ bool flag_get(const uint32_t* __restrict__ fb, int64_
     return (fb[p >> 5] >> (p & 31)) & 1u;
 }
 inline int64_t flag_words(int64_t e2) { return (e2 >> 5) + 4; }
+inline tc_dims dims_of(const tc_graph* g) { return tc_dims{g->n, 2 * g->m, flag_words(2 * g->m)}; }
 
 namespace tcx {
 
@@ -216,16 +282,3 @@ tc_status import_counts(tc_graph* g, const uint64_t* d_tri, const uint8_t* d_fla
 
 }  // namespace tcx
 
-#define TC_TRY(expr)                                    \
-    do {                                                \
-        tc_status _st = (expr);                         \
-        if (_st < 0) return _st;                        \
-    } while (0)
-
-#define TC_CUDA(expr)                                   \
-    do {                                                \
-        cudaError_t _e = (expr);                        \
-        if (_e != cudaSuccess) return tcx::from_cuda(_e); \
-    } while (0)
-
-#define TC_LAUNCH_CHECK() TC_CUDA(cudaGetLastError())

@@ -101,6 +101,7 @@ def test_count_fails_cleanly_at_every_allocation(call, core):
             tcg.tc_count(g.h, tri, flags)
 
     try:
+        run()                  # first call: buffers the graph keeps (edge counts) are made once
         A = allocations_of(run)
         if call == "replan" or core:
             assert A > 0
@@ -119,7 +120,7 @@ def test_count_fails_cleanly_at_every_allocation(call, core):
         numer, tcv, den, _ = g.centrality()
         eu, ev = g.edges()
         check_full(src, dst, n, dict(total=den // 3, tri=tri, numer=numer, tc=tcv,
-                                     flag=(et > 0).to(torch.uint8) if call == "edge_triangles" else flags))
+                                     flag=(et.view(torch.int32) > 0).to(torch.uint8) if call == "edge_triangles" else flags))
     finally:
         g.close()
 
@@ -177,12 +178,12 @@ def test_server_keeps_serving_through_injected_failures():
             ids = {srv.submit(s, d, n): i for i, (s, d, n) in enumerate(reqs)}
             done = srv.wait_all(300)
             assert len(done) == len(reqs)
-            failed = [r for r in done if r["status"] != tcg.TC_OK]
+            failed = [r for r in done if r["status"] < 0]
             assert len(failed) <= 1
             for r in failed:
                 assert r["status"] == tcg.TC_ERR_OUT_OF_MEMORY
             for r in done:
-                if r["status"] == tcg.TC_OK:
+                if r["status"] >= 0:
                     ref = refs[ids[r["id"]]]
                     assert r["triangles"] == ref["total"]
                     np.testing.assert_array_equal(r["tri"].view(np.int64), ref["tri"].astype(np.int64))
@@ -190,6 +191,6 @@ def test_server_keeps_serving_through_injected_failures():
         tcg.tc_debug_fail_allocation(-1)
         ids = {srv.submit(s, d, n): i for i, (s, d, n) in enumerate(reqs)}
         done = srv.wait_all(300)
-        assert len(done) == len(reqs) and all(r["status"] == tcg.TC_OK for r in done)
+        assert len(done) == len(reqs) and all(r["status"] >= 0 for r in done)
     finally:
         srv.close()
