@@ -394,6 +394,24 @@ def run_ours(args, spec, wl_name):
             core_obj = {"kernel": "count_core_pairs", "core_vertices": core_c, "words_per_launch": words,
                         "avg_launch_ms": round(tot_ms / launch_n, 4),
                         "achieved_gwords_per_s": round(words / t_s / 1e9, 1) if t_s > 0 else None}
+        # the build (rows a1-a2) against two byte models: what it must read
+        # and write at least once (pairs in; col, head records, edge_tail,
+        # the canonical edge list, row_ptr/hstart/perm/work out), and what
+        # this implementation moves (the radix passes over 8-byte keys, the
+        # placement and run sorts, the scatter of 16- and 8-byte records at
+        # 32-byte sector granularity)
+        build_ms = sum(v for k, v in kernel_ms.items() if k.startswith(("build", "plan")))
+        bits = max(1, int(n - 1).bit_length())
+        passes = (2 * bits + 7) // 8
+        b_min = 8.0 * np_pairs + 40.0 * m + 28.0 * n
+        b_impl = (24.0 + 16.0 * passes) * np_pairs + 140.0 * m + 28.0 * n
+        build_roof = None
+        if build_ms > 0:
+            build_roof = {"t_ms": round(build_ms, 3), "radix_passes": passes,
+                          "compulsory_bytes": b_min, "compulsory_frac": round(b_min / (build_ms / 1e3) / 1e9 / peak, 4),
+                          "implementation_bytes": b_impl,
+                          "implementation_frac": round(b_impl / (build_ms / 1e3) / 1e9 / peak, 4),
+                          "peak": peak, "unit": "GB/s"}
         cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu) else None
         line = {
             "metric": METRIC,
@@ -434,6 +452,7 @@ def run_ours(args, spec, wl_name):
             "count_plus_centrality_edges_per_s": (m / ((count_ms + gather_ms) / 1e3)) if count_ms else None,
             "roofline_survey_model": survey_roof,
             "dense_core": core_obj,
+            "roofline_build": build_roof,
             "edge_triangles": edge_counts,
             "graph_stats": stats,
         }
@@ -838,7 +857,7 @@ def run_other_configs(args):
     small.no_cpu = True
     small.edge_counts = False
     keep = ("value", "unit", "ms_per_step", "steps", "warmup", "e2e", "gpu_launches", "roofline", "clocks",
-            "phases_ms_per_step", "roofline_survey_model", "dense_core")
+            "phases_ms_per_step", "roofline_survey_model", "dense_core", "roofline_build")
     for name, steps in (("rmat-s12-ef16", max(args.steps, 20)), ("grid4096-diag05-cl21", args.steps)):
         small.steps = steps
         line = run_ours(small, WORKLOADS[name], name)
