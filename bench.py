@@ -66,7 +66,12 @@ def peaks():
 
 # ------------------------------------------------------- DRAM traffic
 COUNT_SOURCES = ["paper_2105_00110_gb300/csrc/tc_count.cu", "paper_2105_00110_gb300/csrc/tc_internal.cuh"]
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "count_dram_traffic_rmat24.md")
+
+
+def traffic_profile(workload: str) -> str:
+    """The committed ncu summary of the count kernels' DRAM traffic on this
+    workload (one kernel, one launch, small enough to capture)."""
+    return os.path.join(ROOT, "profiles", "count_dram_traffic_%s.md" % workload)
 
 
 def count_sources_sha() -> str:
@@ -83,7 +88,7 @@ def dram_traffic(kernel: str, workload: str):
     from the committed ncu summary, or None when that summary is for other
     count-kernel sources or another workload."""
     try:
-        with open(TRAFFIC_PROFILE) as fh:
+        with open(traffic_profile(workload)) as fh:
             text = fh.read()
     except OSError:
         return None

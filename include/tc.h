@@ -272,7 +272,8 @@ tc_status tc_set_strategy(tc_graph* g, int strategy);
  * vertex may become CTA items, params3[1] = target wedges per CTA item (a
  * heavy vertex is split into chunks of about this size; each chunk stages
  * N_H(v) again), params3[2] = the same for warp items.  The next tc_count
- * re-plans.  Defaults 4096, 4194304, 32768.
+ * re-plans.  Defaults 4096, a CTA chunk of the graph's wedges / (64 · SMs)
+ * within [65536, 4194304] (set by the build), and 32768.
  */
 tc_status tc_set_plan_params(tc_graph* g, const int64_t* params3);
 tc_status tc_get_plan_params(const tc_graph* g, int64_t* out3);

@@ -520,7 +520,7 @@ tc_status build_runs(tc_graph* g, cudaStream_t s, int64_t m, int64_t n, int bits
 void free_graph_memory(tc_graph* g) {
     cudaStream_t s = g->stream;
     void* ptrs[] = {g->edge_u, g->edge_v, g->perm, g->row_ptr, g->col, g->hstart, g->head,
-                    g->edge_tail, g->work, g->tri, g->flag, g->numer, g->counters, g->ecnt};
+                    g->edge_tail, g->work, g->tri, g->flag, g->tri32, g->counters, g->ecnt};
     for (void* q : ptrs) dfree(q, s);
     free_plan(g->plan, s);
 }
@@ -618,7 +618,7 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
     TC_TRY(dalloc((void**)&g->head, (e2 + 1) * sizeof(tc_head), s));
     TC_TRY(dalloc((void**)&g->edge_tail, (m + 1) * 8, s));
     TC_TRY(dalloc((void**)&g->tri, (n + 1) * 8, s));
-    TC_TRY(dalloc((void**)&g->numer, (n + 1) * 8, s));
+    TC_TRY(dalloc((void**)&g->tri32, (n + 1) * 4, s));
     TC_TRY(dalloc((void**)&g->flag, flag_words(e2) * 4, s));
     TC_TRY(dalloc((void**)&g->counters, 8 * 8, s));
 
@@ -785,10 +785,20 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
     // (4 W), write the vertex counts (8n) and one flag byte per tail entry (m).
     S.count_bytes = 4.0 * m + 16.0 * m + 4.0 * S.wedges + 8.0 * n + 1.0 * m;
     // Gather: per vertex row_ptr, hstart, perm, △(v), numerator and TC out
-    // (8+8+4+8+8+8); per adjacency entry its label and the neighbour's count
-    // (4+8); per head entry twin and the mirrored flag (8+1); per tail entry
+    // (8+8+4+8+8+8) and the 32-bit copy of △(v) made first (8 in, 4 out); per
+    // adjacency entry its label and the neighbour's count from that copy
+    // (4+4); per head entry twin and the mirrored flag (8+1); per tail entry
     // its flag (1).
-    S.centrality_bytes = 44.0 * n + 12.0 * (double)e2 + 9.0 * m + 1.0 * m;
+    S.centrality_bytes = 56.0 * n + 8.0 * (double)e2 + 9.0 * m + 1.0 * m;
+    // Target work of a CTA item: large items stage N_H(v) less often, small
+    // ones spread a few heavy vertices over more CTAs.  About 64 items' worth
+    // of the graph's wedges per SM, within [2^16, 2^22] (R-MAT scale 24: 2^22;
+    // the 4096^2 grid with its Chung-Lu hubs: 2^16, where 2^22 left the
+    // bitmap kernel 2.5 times slower).  tc_set_plan_params overrides it.
+    {
+        const double per = S.wedges / (64.0 * (double)sm_count());
+        g->params.cta_chunk = (int64_t)std::min(4194304.0, std::max(65536.0, per));
+    }
     TC_TRY(make_plan(g, g->strategy, s));
     TC_CUDA(cudaStreamSynchronize(s));
     return TC_OK;

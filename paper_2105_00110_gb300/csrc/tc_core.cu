@@ -57,9 +57,9 @@ constexpr int kFillThreads = 256;
 // Rough rates, used only to decide whether a core pays: ids streamed per
 // ms by the bitmap count kernel (R-MAT scale 24: the 1.0e10 ids of the top
 // 16384 ranks took 10 ms), and row words ANDed per ms by k_core_pairs
-// (R-MAT scales 22 and 24: 2.6e9 - 3.2e9).
+// (R-MAT scales 22 and 24: 2.8e9 - 4.3e9).
 constexpr double kStreamIdsPerMs = 1.0e9;
-constexpr double kWordsPerMs = 3.0e9;
+constexpr double kWordsPerMs = 3.5e9;
 constexpr double kFixedMs = 0.1;       // fill, staging, launches
 constexpr double kMinGainMs = 0.5;
 
@@ -238,26 +238,26 @@ k_core_pairs(const uint32_t* __restrict__ R, const uint16_t* __restrict__ P, con
             if (!mask) continue;
             const int vw = (int)(v >> 5);
             const uint32_t below_v = (1u << (v & 31)) - 1u;
-            uint32_t vsum = 0;
+            uint32_t vsum = 0, myT = 0;   // myT: T(u0 + lane, v) for this lane's u
             while (mask) {
                 const int b = __ffs(mask) - 1;
                 mask &= mask - 1;
                 const uint4* ru = (const uint4*)(Rs + b * W);
                 const uint32_t T = __reduce_add_sync(0xffffffffu, and_popc<KW>(ru, rv, lane));
-                if (T) {
-                    vsum += T;
-                    if (lane == 0) {
-                        const int64_t u = u0 + b;
-                        atomicAdd(&Su[b], T);
-                        // tail position of (u, v): v's place in N_H(u)
-                        const int uiw = (int)(u >> 5);
-                        const uint32_t gt = vw > uiw ? 0xffffffffu : ~((2u << (u & 31)) - 1u);
-                        const int64_t pos = Hs[b] + Ps[b * W + vw] + __popc(Rs[b * W + vw] & below_v & gt);
-                        // fire-and-forget updates: nothing here waits on a global load
-                        if (ecnt) atomicAdd(&ecnt[TC_IX(pos, dm.e2)], T);
-                        else atomicOr(&flag[TC_IX(pos >> 5, dm.fw)], 1u << (pos & 31));
-                    }
-                }
+                vsum += T;
+                if (lane == b) myT = T;
+            }
+            // the edges of this v with T > 0, one lane each: the per-vertex
+            // sum at u, and the flag of (u, v) at its tail position — v's
+            // place in N_H(u) — as fire-and-forget updates
+            if (myT) {
+                const int64_t u = u0 + lane;
+                atomicAdd(&Su[lane], myT);
+                const int uiw = (int)(u >> 5);
+                const uint32_t gt = vw > uiw ? 0xffffffffu : ~((2u << (u & 31)) - 1u);
+                const int64_t pos = Hs[lane] + Ps[lane * W + vw] + __popc(Rs[lane * W + vw] & below_v & gt);
+                if (ecnt) atomicAdd(&ecnt[TC_IX(pos, dm.e2)], myT);
+                else atomicOr(&flag[TC_IX(pos >> 5, dm.fw)], 1u << (pos & 31));
             }
             if (lane == 0 && vsum) {
                 atomicAdd(&S[TC_IX(v, C)], (ull)vsum);

@@ -85,25 +85,36 @@ struct gather_args {
     ull den;
     const int32_t* rank_graph;   // batches: graph of each rank, or null
     const ull* den_graph;        // batches: 3△ of each graph
-    ull* numer_rank;
+    const uint32_t* tri32;       // △ in 32 bits (half the size of tri: stays in L2), or the
+                                 // escape 0xffffffff where △ >= 2^32
     ull* numer_out;
     double* tc_out;
     tc_dims dm;
 };
+
+// △(u) of a neighbour: the 32-bit copy, or the full count behind its escape.
+__device__ __forceinline__ ull tri_of(const gather_args& a, int32_t u) {
+    const uint32_t t = a.tri32[TC_IX(u, a.dm.n)];
+    return t != 0xffffffffu ? (ull)t : a.tri[TC_IX(u, a.dm.n)];
+}
 
 // One adjacency entry's term (flag ? 1 : 3)·△(u): a head entry's record
 // gives u and the twin position holding its flag, a tail entry holds u in
 // col and its flag in place.
 __device__ __forceinline__ ull head_term(const gather_args& a, int64_t p) {
     const tc_head rec = a.head[TC_IX(p, a.dm.e2)];
-    return (flag_get(a.flag, TC_IX(rec.twin, a.dm.fw * 32)) ? 1ull : 3ull) * a.tri[TC_IX(rec.u, a.dm.n)];
+    return (flag_get(a.flag, TC_IX(rec.twin, a.dm.fw * 32)) ? 1ull : 3ull) * tri_of(a, rec.u);
 }
 __device__ __forceinline__ ull tail_term(const gather_args& a, int64_t p) {
-    return (flag_get(a.flag, TC_IX(p, a.dm.fw * 32)) ? 1ull : 3ull) * a.tri[TC_IX(a.col[TC_IX(p, a.dm.e2)], a.dm.n)];
+    return (flag_get(a.flag, TC_IX(p, a.dm.fw * 32)) ? 1ull : 3ull) * tri_of(a, a.col[TC_IX(p, a.dm.e2)]);
+}
+
+__global__ void k_tri32(const ull* __restrict__ tri, int64_t n, uint32_t* __restrict__ tri32) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        tri32[r] = tri[r] < 0xffffffffull ? (uint32_t)tri[r] : 0xffffffffu;
 }
 
 __device__ __forceinline__ void finish_row(int64_t r, ull acc, const gather_args& a) {
-    a.numer_rank[r] = acc;
     const int32_t v = a.perm[TC_IX(r, a.dm.n)];
     if (a.numer_out) a.numer_out[v] = acc;
     if (a.tc_out) a.tc_out[v] = div_rn(acc, a.rank_graph ? a.den_graph[a.rank_graph[r]] : a.den);
@@ -234,8 +245,13 @@ tc_status run_centrality(tc_graph* g, uint64_t* d_numer, double* d_tc, cudaStrea
     const int64_t n = g->n;
     if (n == 0) return TC_OK;
     gather_args a{g->row_ptr, g->hstart, g->col, g->head, g->flag, g->tri, g->perm,
-                  3ull * (ull)g->total, g->rank_graph, g->den_graph, g->numer, (ull*)d_numer, d_tc,
+                  3ull * (ull)g->total, g->rank_graph, g->den_graph, g->tri32, (ull*)d_numer, d_tc,
                   dims_of(g)};
+    {
+        launch_scope ls("gather_tri32", s);
+        k_tri32<<<blocks_for(n, 256), 256, 0, s>>>(g->tri, n, g->tri32);
+        TC_LAUNCH_CHECK();
+    }
     const int64_t r1 = g->band[0], r2 = g->band[1];   // degree <= 32 | <= 4096 | larger
     if (r1 > 0) {
         launch_scope ls("gather_thread", s);

@@ -58,7 +58,8 @@ struct __align__(16) tc_head {
 // Planner parameters (tuned per batch by tc_batch_autotune).
 struct tc_plan_params {
     int64_t cta_min_work = 4096;   // W(v) at or above which v may become CTA items
-    int64_t cta_chunk = 4194304;   // target wedges per CTA item (each chunk re-stages N_H(v))
+    int64_t cta_chunk = 4194304;   // target wedges per CTA item (each chunk re-stages N_H(v));
+                                   // the build sets it from the graph's wedges
     int64_t warp_chunk = 32768;    // target wedges per warp item
 };
 
@@ -93,7 +94,8 @@ struct tc_graph {
     unsigned long long* tri = nullptr;   // [n], rank space
     uint32_t* flag = nullptr;            // one bit per CSR position (2m bits), set on tail entries
     uint32_t* ecnt = nullptr;            // [2m] triangles on each tail entry (edge-count mode only)
-    unsigned long long* numer = nullptr; // [n], rank space
+    uint32_t* tri32 = nullptr;           // [n], rank space: △(v) for the gather's neighbour
+                                         // reads, 0xffffffff where △(v) >= 2^32 (then read tri)
     unsigned long long* counters = nullptr;  // [8]: 0 total, 1 warp cursor, 2 cta cursor
     int counted = 0;
     uint64_t total = 0;

@@ -230,7 +230,10 @@ def test_planner_settings_change_no_result():
     s, d, n = gg.rmat(15, seed=0x5EED0300)
     g = tcg.Graph(torch.from_numpy(s).cuda(), torch.from_numpy(d).cuda(), n)
     try:
-        assert tcg.tc_get_plan_params(g.h) == dict(cta_min_work=4096, cta_chunk=4194304, warp_chunk=32768)
+        # the default CTA chunk follows the graph's wedges: wedges / (64 SMs), within [2^16, 2^22]
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        chunk = int(min(4194304.0, max(65536.0, g.stats()["wedges"] / (64.0 * sms))))
+        assert tcg.tc_get_plan_params(g.h) == dict(cta_min_work=4096, cta_chunk=chunk, warp_chunk=32768)
         runs = []
         for params in ((4096, 4194304, 32768), (256, 1024, 512), (1 << 40, 1 << 40, 1 << 40), (0, 1, 1)):
             tcg.tc_set_plan_params(g.h, *params)
