@@ -114,6 +114,27 @@ struct lookup_sorted {
     }
 };
 
+// N_H(v) as an ascending list behind a hashed filter: one bit per slot of a
+// table of kFilterBits slots, set for the slot of every staged id.  An id
+// whose slot is clear is not staged, which one shared load settles; only
+// the others are bisected.  Light middle vertices (the warp items) have
+// id windows far too wide for a bitmap, and almost every streamed id
+// misses their N_H(v) (2 % hits at R-MAT scale 20), so the filter takes
+// the bisection off nearly every id.
+#ifndef TC_FILTER_LOG2
+#define TC_FILTER_LOG2 12
+#endif
+constexpr int kFilterBits = 1 << TC_FILTER_LOG2;
+constexpr int kFilterWords = kFilterBits / 32;
+// Fibonacci hashing: the top bits of the id times 2^32 / golden ratio
+__device__ __forceinline__ uint32_t filter_slot(int32_t w) {
+    return ((uint32_t)w * 0x9E3779B1u) >> (32 - TC_FILTER_LOG2);
+}
+struct lookup_filtered {
+    lookup_sorted ls;
+    const uint32_t* filt;
+};
+
 // N_H(v) read in place from global memory (lists too long for shared memory).
 struct lookup_global {
     const int32_t* ids;
@@ -377,6 +398,38 @@ __device__ __forceinline__ uint32_t visit_octet_bitmap(const lookup_bitmap& lk, 
     return (uint32_t)__popc(hm);
 }
 
+// The filtered sorted list: the 8 filter bits first, then the bisection of
+// the ids whose slot is set, one at a time per lane (a lane's candidates
+// are few, so the warp runs the bisection once or twice per octet rather
+// than once per id).
+template <bool EC>
+__device__ __forceinline__ uint32_t visit_octet_filtered(const lookup_filtered& lk, const octet& o, int64_t pos,
+                                                         int off, int len, uint32_t* cnt,
+                                                         uint32_t* __restrict__ flag, const tc_dims& dm) {
+    uint32_t cand = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t h = filter_slot(o.x[k]);
+        cand |= ((lk.filt[h >> 5] >> (h & 31)) & 1u) << k;
+    }
+    cand &= octet_valid(off, len);
+    uint32_t hm = 0;
+    while (cand) {
+        const int k = __ffs(cand) - 1;
+        cand &= cand - 1;
+        int32_t w = o.x[0];
+#pragma unroll
+        for (int j = 1; j < 8; ++j) w = k == j ? o.x[j] : w;
+        int l = 0;
+        if (lk.ls.find(w, l)) {
+            atomicAdd(&cnt[TC_IX(l, lk.ls.hv)], 1u);
+            hm |= 1u << k;
+        }
+    }
+    mark_octet<EC>(flag, pos, hm, dm);
+    return (uint32_t)__popc(hm);
+}
+
 // Walks the groups [gb, ge) of the concatenated streams of a table (nc
 // streams), one group of G octets per lane per window.  The stream of each
 // lane is found from the starts of the next 32 streams that fall inside the
@@ -417,6 +470,8 @@ __device__ __forceinline__ void walk_groups(int lane, stream_table<N>& tb, int n
             for (int j = 0; j < G; ++j)
                 if constexpr (std::is_same<LK, lookup_bitmap>::value && CNT)
                     h += visit_octet_bitmap<EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, h0, tri, flag, dm);
+                else if constexpr (std::is_same<LK, lookup_filtered>::value)
+                    h += visit_octet_filtered<EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, flag, dm);
                 else
                     h += visit_octet<LK, CNT, EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, h0, tri, flag, dm);
         }
@@ -477,10 +532,14 @@ __device__ __forceinline__ void merge_streams(int lane, int k0, int k1, stream_t
 constexpr int kWarpSmem = 8 * TC_WARP_CAP;
 struct warp_smem {
     uint8_t region[kWarpSmem];
+    uint32_t filt[kFilterWords];
     stream_table<32> tb;
 };
 #ifndef TC_WARP_FETCH
 #define TC_WARP_FETCH 2
+#endif
+#ifndef TC_WARP_FILTER
+#define TC_WARP_FILTER 1
 #endif
 constexpr int kWarpItemsPerFetch = TC_WARP_FETCH;
 
@@ -544,6 +603,9 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
             const int hv = (int)(h1 - h0);
             const int32_t nbits = col[TC_IX(h1 - 1, dm.e2)] - v;
             const bool use_bitmap = allow_bitmap && warp_bitmap_fits((nbits + 31) >> 5, hv);
+            // the filter in front of the bisection: automatic strategy only,
+            // so that a forced binary search still bisects every id
+            const bool use_filter = !MERGE && !use_bitmap && TC_WARP_FILTER && strategy == TC_STRATEGY_AUTO;
             uint32_t* cnt;
             lookup_bitmap lb{};
             int32_t* ids = (int32_t*)ws.region;
@@ -551,13 +613,22 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
                 lb = build_bitmap(lane, 32, ws.region, v, h0, hv, nbits, col, cnt, wbar, nullptr, lane, 0, 1, dm);
             } else {
                 cnt = (uint32_t*)(ids + TC_WARP_CAP);
+                if (use_filter)
+                    for (int i = lane; i < kFilterWords; i += 32) ws.filt[i] = 0;
+                __syncwarp();
                 for (int i = lane; i < hv; i += 32) {
-                    ids[TC_IX(i, TC_WARP_CAP)] = col[TC_IX(h0 + i, dm.e2)];
+                    const int32_t x = col[TC_IX(h0 + i, dm.e2)];
+                    ids[TC_IX(i, TC_WARP_CAP)] = x;
                     cnt[TC_IX(i, TC_WARP_CAP)] = 0;
+                    if (use_filter) {
+                        const uint32_t h = filter_slot(x);
+                        atomicOr(&ws.filt[h >> 5], 1u << (h & 31));
+                    }
                 }
                 __syncwarp();
             }
             const lookup_sorted ls{ids, hv};
+            const lookup_filtered lf{ls, ws.filt};
             ull tv = 0;
             for (int64_t b = pb; b < pe; b += 32) {
                 const entry cur = nxt;
@@ -566,6 +637,7 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
                 const int groups = compact_warp<kWarpG>(lane, cur, ws.tb, nc);
                 if (MERGE) merge_streams<32, EC>(lane, 0, nc, ws.tb, ids, hv, cnt, col, flag, dm);
                 else if (use_bitmap) walk_groups<lookup_bitmap, true, 32, kWarpG, EC>(lane, ws.tb, nc, 0, groups, lb, cnt, h0, col, tri, flag, dm);
+                else if (use_filter) walk_groups<lookup_filtered, true, 32, kWarpG, EC>(lane, ws.tb, nc, 0, groups, lf, cnt, h0, col, tri, flag, dm);
                 else walk_groups<lookup_sorted, true, 32, kWarpG, EC>(lane, ws.tb, nc, 0, groups, ls, cnt, h0, col, tri, flag, dm);
                 __syncwarp();
                 if (lane < nc) close_stream<32, EC>(lane, ws.tb, tri, flag, tv, dm);
