@@ -29,7 +29,8 @@
 // the window (one warp OR-reduction).
 //
 // Item classes (planner below): CTA bitmaps of two shared sizes, warp
-// items (bitmap or sorted list), CTA sorted lists (shared or global), and
+// items (bitmap, or sorted list behind a hashed filter), CTA sorted lists
+// (shared or global), and
 // one thread per tiny vertex.  Two switches ride along every kernel: the
 // edge-count mode (EC), which adds per-entry triangle counts where the
 // normal mode sets flag bits, and an item offset/stride, which restricts a
@@ -122,13 +123,20 @@ struct lookup_sorted {
 // misses their N_H(v) (2 % hits at R-MAT scale 20), so the filter takes
 // the bisection off nearly every id.
 #ifndef TC_FILTER_LOG2
-#define TC_FILTER_LOG2 12
+#define TC_FILTER_LOG2 13
 #endif
 constexpr int kFilterBits = 1 << TC_FILTER_LOG2;
 constexpr int kFilterWords = kFilterBits / 32;
-// Fibonacci hashing: the top bits of the id times 2^32 / golden ratio
+#ifndef TC_FILTER_HASHES
+#define TC_FILTER_HASHES 2
+#endif
+// Fibonacci hashing: the top bits of the id times 2^32 / golden ratio (a
+// second slot, with TC_FILTER_HASHES 2, from another odd multiplier)
 __device__ __forceinline__ uint32_t filter_slot(int32_t w) {
     return ((uint32_t)w * 0x9E3779B1u) >> (32 - TC_FILTER_LOG2);
+}
+__device__ __forceinline__ uint32_t filter_slot2(int32_t w) {
+    return ((uint32_t)w * 0x85EBCA6Bu) >> (32 - TC_FILTER_LOG2);
 }
 struct lookup_filtered {
     lookup_sorted ls;
@@ -410,7 +418,12 @@ __device__ __forceinline__ uint32_t visit_octet_filtered(const lookup_filtered& 
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const uint32_t h = filter_slot(o.x[k]);
-        cand |= ((lk.filt[h >> 5] >> (h & 31)) & 1u) << k;
+        uint32_t bit = (lk.filt[h >> 5] >> (h & 31)) & 1u;
+        if (TC_FILTER_HASHES > 1) {
+            const uint32_t h2 = filter_slot2(o.x[k]);
+            bit &= (lk.filt[h2 >> 5] >> (h2 & 31)) & 1u;
+        }
+        cand |= bit << k;
     }
     cand &= octet_valid(off, len);
     uint32_t hm = 0;
@@ -623,6 +636,10 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
                     if (use_filter) {
                         const uint32_t h = filter_slot(x);
                         atomicOr(&ws.filt[h >> 5], 1u << (h & 31));
+                        if (TC_FILTER_HASHES > 1) {
+                            const uint32_t h2 = filter_slot2(x);
+                            atomicOr(&ws.filt[h2 >> 5], 1u << (h2 & 31));
+                        }
                     }
                 }
                 __syncwarp();
@@ -803,6 +820,10 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
 constexpr int kThreadMaxH = TC_THREAD_MAX_H;      // staged ids per thread (a column of S)
 constexpr int64_t kThreadMaxWork = TC_THREAD_MAX_WORK;
 constexpr int kThreadBlock = TC_THREAD_BLOCK;     // threads of the thread-item kernel
+#ifndef TC_THREAD_ILP
+#define TC_THREAD_ILP 4
+#endif
+constexpr int kThreadILP = TC_THREAD_ILP;         // independent loads in flight per thread
 static_assert(kThreadMaxH * kThreadBlock * 4 <= 48 * 1024, "thread-item staging exceeds static shared memory");
 
 template <bool EC>
@@ -821,11 +842,23 @@ k_count_thread(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ 
         const int32_t v = it_v[gi];
         const int64_t h0 = hstart[TC_IX(v, dm.n)], h1 = row_ptr[TC_IX(v, dm.n) + 1];
         const int hv = (int)(h1 - h0);
-        for (int k = 0; k < hv; ++k) S[TC_IX(k, kThreadMaxH)][t] = col[TC_IX(h0 + k, dm.e2)];
+        // loads issued kThreadILP at a time, so that one thread's chain of
+        // small reads does not wait for each in turn
+        for (int k0 = 0; k0 < hv; k0 += kThreadILP) {
+            int32_t x[kThreadILP];
+#pragma unroll
+            for (int j = 0; j < kThreadILP; ++j) x[j] = k0 + j < hv ? col[TC_IX(h0 + k0 + j, dm.e2)] : 0;
+#pragma unroll
+            for (int j = 0; j < kThreadILP; ++j)
+                if (k0 + j < hv) S[TC_IX(k0 + j, kThreadMaxH)][t] = x[j];
+        }
         ull tv = 0;
-        const int64_t pe = it_pe[gi];
-        for (int64_t p = it_pb[gi]; p < pe; ++p) {
-            const tc_head rec = head[TC_IX(p, dm.e2)];
+        const int64_t pb = it_pb[gi], pe = it_pe[gi];
+        tc_head nrec{};
+        if (pb < pe) nrec = head[TC_IX(pb, dm.e2)];
+        for (int64_t p = pb; p < pe; ++p) {
+            const tc_head rec = nrec;
+            if (p + 1 < pe) nrec = head[TC_IX(p + 1, dm.e2)];   // in flight meanwhile
             const int64_t q0 = rec.twin + 1;
             const int len = rec.hrem;
             uint32_t hits = 0;
@@ -844,15 +877,23 @@ k_count_thread(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ 
                     }
                 }
             }
-            for (int j = 0; j < len && a < hv; ++j) {
-                const int32_t w = col[TC_IX(q0 + j, dm.e2)];
-                while (a < hv && S[a][t] < w) ++a;
-                if (a < hv && S[a][t] == w) {
-                    atomicAdd(&tri[TC_IX(w, dm.n)], 1ull);
-                    mark<EC>(flag, q0 + j, 1u, dm);
-                    mark<EC>(flag, h0 + a, 1u, dm);
-                    ++hits;
-                    ++a;
+            for (int j0 = 0; j0 < len && a < hv; j0 += kThreadILP) {
+                int32_t wv[kThreadILP];
+#pragma unroll
+                for (int j = 0; j < kThreadILP; ++j) wv[j] = j0 + j < len ? col[TC_IX(q0 + j0 + j, dm.e2)] : 0;
+#pragma unroll
+                for (int j = 0; j < kThreadILP; ++j) {
+                    const int32_t w = wv[j];
+                    if (j0 + j < len) {
+                        while (a < hv && S[a][t] < w) ++a;
+                        if (a < hv && S[a][t] == w) {
+                            atomicAdd(&tri[TC_IX(w, dm.n)], 1ull);
+                            mark<EC>(flag, q0 + j0 + j, 1u, dm);
+                            mark<EC>(flag, h0 + a, 1u, dm);
+                            ++hits;
+                            ++a;
+                        }
+                    }
                 }
             }
             if (hits) {
