@@ -324,6 +324,7 @@ tc_status tc_batch_autotune(tc_batch* b, int reps, tc_stream stream) {
     tc_status st = TC_OK;
     for (const tc_plan_params& c : cands) {
         g->params = c;
+        g->params.thread_work = best_p.thread_work;   // not one of the tuned settings
         g->params_version += 1;
         st = run_count(g, s);   // re-plans for the new parameters, then warms up
         if (st < 0) break;
@@ -339,7 +340,7 @@ tc_status tc_batch_autotune(tc_batch* b, int reps, tc_stream stream) {
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best) {
             best = ms;
-            best_p = c;
+            best_p = g->params;
         }
     }
     cudaEventDestroy(e0);

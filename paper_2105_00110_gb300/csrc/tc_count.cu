@@ -802,15 +802,12 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
 
 // ------------------------------------------------------------ thread items
 // Tiny middle vertices (|N_H(v)| <= kThreadMaxH, head entries + streamed
-// ids <= kThreadMaxWork) take one thread each: N_H(v) is staged in the
+// ids <= the planner's thread_work) take one thread each: N_H(v) is staged in the
 // thread's own column of shared memory (S[k][t], so that the threads of a
 // warp hit distinct banks), and every stream of the vertex is merged
 // against it.  A hit at staged index a and stream position q is the
 // triangle (u, v, w): △(w) += 1, edges (u, w) at q and (v, w) at h0 + a
 // marked, then per stream △(u) and edge (u, v) at twin, per vertex △(v).
-#ifndef TC_THREAD_MAX_WORK
-#define TC_THREAD_MAX_WORK 64
-#endif
 #ifndef TC_THREAD_MAX_H
 #define TC_THREAD_MAX_H 32
 #endif
@@ -818,7 +815,6 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
 #define TC_THREAD_BLOCK 256
 #endif
 constexpr int kThreadMaxH = TC_THREAD_MAX_H;      // staged ids per thread (a column of S)
-constexpr int64_t kThreadMaxWork = TC_THREAD_MAX_WORK;
 constexpr int kThreadBlock = TC_THREAD_BLOCK;     // threads of the thread-item kernel
 #ifndef TC_THREAD_ILP
 #define TC_THREAD_ILP 4
@@ -950,7 +946,7 @@ __global__ void k_classify(const int64_t* __restrict__ row_ptr, const int64_t* _
                 // bitmap when zeroing it is cheap next to the work; the rest
                 // on a warp (bitmap or list)
                 const bool heavy = W >= pp.cta_min_work && W >= 2 * words;
-                if (hv <= kThreadMaxH && lv + W <= kThreadMaxWork) c = TC_CLS_THREAD;
+                if (hv <= kThreadMaxH && lv + W <= pp.thread_work) c = TC_CLS_THREAD;
                 else if (heavy && cta_s) c = TC_CLS_BITMAP_S;
                 else if (heavy && cta_l) c = TC_CLS_BITMAP_L;
                 else if (warp_bm || warp_list) c = TC_CLS_WARP;

@@ -61,6 +61,9 @@ struct tc_plan_params {
     int64_t cta_chunk = 4194304;   // target wedges per CTA item (each chunk re-stages N_H(v));
                                    // the build sets it from the graph's wedges
     int64_t warp_chunk = 32768;    // target wedges per warp item
+    int64_t thread_work = 64;      // head entries + streamed ids at or below which a vertex
+                                   // with |N_H(v)| <= 32 is one thread's item (unions of many
+                                   // graphs: 128, set by the build)
 };
 
 struct tc_plan {
