@@ -7,7 +7,9 @@ automatic strategy), where the oracle is too slow to run whole:
   △(v), canonical edges and per-edge counts;
 - everywhere, identities that hold at any size: Σ△ = 3△(G), Σ t = 3△(G),
   △(v) = ½ Σ_u t(v, u), flag = [t > 0], the two count modes agree, and the
-  numerator and the correctly rounded TC recomputed from △ and the flags."""
+  numerator and the correctly rounded TC recomputed from △ and the flags;
+- and, on R-MAT scale 22 and the whole 4096² grid, every output against
+  the whole oracle run on the host's threads."""
 from __future__ import annotations
 
 import numpy as np
@@ -98,3 +100,24 @@ def test_full_size(workload):
     r = gpu_path(s, d, n)
     check_identities(r)
     check_samples(r, s, d, n, seed=0x5EED)
+
+
+@pytest.mark.parametrize("workload", ["rmat-s22-ef16", "grid4096-diag05-cl21"])
+def test_whole_graph_against_threaded_oracle(workload):
+    # every vertex and edge of a large workload against the whole oracle:
+    # its degree-ordered listing (pinned against the definition) run on the
+    # host's threads; △(v), flags, t(u, v), numerators and TC all bit for bit
+    import os
+    s, d, n = bench.generate(bench.WORKLOADS[workload])
+    r = gpu_path(s, d, n)
+    ref = oracle.run(s, d, n, "fast", threads=os.cpu_count() or 1, algebraic=False)
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(ref["ptr"]))
+    keep = ref["adj"] > rows
+    assert r["total"] == ref["total"] and r["m"] == int(keep.sum())
+    assert np.array_equal(r["eu"].cpu().numpy(), rows[keep])
+    assert np.array_equal(r["ev"].cpu().numpy(), ref["adj"][keep].astype(np.int64))
+    assert np.array_equal(r["tri"].cpu().numpy(), ref["tri"].astype(np.int64))
+    assert np.array_equal(r["flags"].cpu().numpy(), ref["flag"][keep])
+    assert np.array_equal(r["et"].cpu().numpy(), ref["t"][keep].astype(np.int64))
+    assert np.array_equal(r["numer"].cpu().numpy(), ref["numer"].astype(np.int64))
+    assert np.array_equal(r["tc"].cpu().numpy().view(np.int64), ref["tc"].view(np.int64))
