@@ -370,11 +370,10 @@ __device__ __forceinline__ uint32_t octet_valid(int off, int len) {
     return hi > lo ? (0xffu >> (8 - hi)) & (0xffu << lo) : 0u;
 }
 
-template <bool EC>
-__device__ __forceinline__ uint32_t visit_octet_bitmap(const lookup_bitmap& lk, const octet& o, int64_t pos,
-                                                       int off, int len, uint32_t* cnt, int64_t h0,
-                                                       ull* __restrict__ tri, uint32_t* __restrict__ flag,
-                                                       const tc_dims& dm) {
+// The hit mask of one octet against a bitmap staging, with the hits counted
+// at their staged indices; the caller sets the octet's flags.
+__device__ __forceinline__ uint32_t octet_hits_bitmap(const lookup_bitmap& lk, const octet& o, int off, int len,
+                                                      uint32_t* cnt) {
     uint32_t word[8], boff[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -402,8 +401,35 @@ __device__ __forceinline__ uint32_t visit_octet_bitmap(const lookup_bitmap& lk, 
 #pragma unroll
     for (int k = 0; k < 8; ++k)
         if ((hm >> k) & 1u) atomicAdd(&cnt[TC_IX(l[k], lk.hv)], 1u);
+    return hm;
+}
+
+template <bool EC>
+__device__ __forceinline__ uint32_t visit_octet_bitmap(const lookup_bitmap& lk, const octet& o, int64_t pos,
+                                                       int off, int len, uint32_t* cnt, int64_t h0,
+                                                       ull* __restrict__ tri, uint32_t* __restrict__ flag,
+                                                       const tc_dims& dm) {
+    const uint32_t hm = octet_hits_bitmap(lk, o, off, len, cnt);
     mark_octet<EC>(flag, pos, hm, dm);
     return (uint32_t)__popc(hm);
+}
+
+// The G octets of a lane (8 G ids from the 8-aligned position pos) lie in at
+// most two 32-bit flag words when 8 G + 24 <= 64: their hit masks are put
+// side by side and each word gets one OR.
+#ifndef TC_FLAG_COMBINE
+#define TC_FLAG_COMBINE 1
+#endif
+template <int G>
+__device__ __forceinline__ uint32_t mark_group(uint32_t* __restrict__ f, int64_t pos, uint64_t hm,
+                                               const tc_dims& dm) {
+    static_assert(8 * G + 24 <= 64, "a lane's octets span more than two flag words");
+    if (hm == 0) return 0;
+    const uint64_t wm = hm << (pos & 31);
+    const int64_t w0 = pos >> 5;
+    if ((uint32_t)wm) flag_or(f, TC_IX(w0, dm.fw), (uint32_t)wm);
+    if ((uint32_t)(wm >> 32)) flag_or(f, TC_IX(w0 + 1, dm.fw), (uint32_t)(wm >> 32));
+    return (uint32_t)__popcll(hm);
 }
 
 // The filtered sorted list: the 8 filter bits first, then the bisection of
@@ -443,6 +469,32 @@ __device__ __forceinline__ uint32_t visit_octet_filtered(const lookup_filtered& 
     return (uint32_t)__popc(hm);
 }
 
+// The G octets of one lane at the 8-aligned position pos (the first id at
+// offset off0 from its stream start, len ids in the stream).  Returns the hits.
+template <class LK, bool CNT, int G, bool EC>
+__device__ __forceinline__ uint32_t visit_group(const LK& lk, const octet (&o)[G], int64_t pos, int off0, int len,
+                                                uint32_t* cnt, int64_t h0, ull* __restrict__ tri,
+                                                uint32_t* __restrict__ flag, const tc_dims& dm) {
+    uint32_t h = 0;
+    if constexpr (std::is_same<LK, lookup_bitmap>::value && CNT && !EC && TC_FLAG_COMBINE && G > 1) {
+        uint64_t hm = 0;
+#pragma unroll
+        for (int j = 0; j < G; ++j) hm |= (uint64_t)octet_hits_bitmap(lk, o[j], off0 + 8 * j, len, cnt) << (8 * j);
+        h = mark_group<G>(flag, pos, hm, dm);
+    } else {
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if constexpr (std::is_same<LK, lookup_bitmap>::value && CNT)
+                h += visit_octet_bitmap<EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, h0, tri, flag, dm);
+            else if constexpr (std::is_same<LK, lookup_filtered>::value)
+                h += visit_octet_filtered<EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, flag, dm);
+            else
+                h += visit_octet<LK, CNT, EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, h0, tri, flag, dm);
+        }
+    }
+    return h;
+}
+
 // Walks the groups [gb, ge) of the concatenated streams of a table (nc
 // streams), one group of G octets per lane per window.  The stream of each
 // lane is found from the starts of the next 32 streams that fall inside the
@@ -479,14 +531,7 @@ __device__ __forceinline__ void walk_groups(int lane, stream_table<N>& tb, int n
             octet o[G];
 #pragma unroll
             for (int j = 0; j < G; ++j) o[j] = load8(col, TC_IX(pos + 8 * j, dm.e2 + 25));
-#pragma unroll
-            for (int j = 0; j < G; ++j)
-                if constexpr (std::is_same<LK, lookup_bitmap>::value && CNT)
-                    h += visit_octet_bitmap<EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, h0, tri, flag, dm);
-                else if constexpr (std::is_same<LK, lookup_filtered>::value)
-                    h += visit_octet_filtered<EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, flag, dm);
-                else
-                    h += visit_octet<LK, CNT, EC>(lk, o[j], pos + 8 * j, off0 + 8 * j, len, cnt, h0, tri, flag, dm);
+            h = visit_group<LK, CNT, G, EC>(lk, o, pos, off0, len, cnt, h0, tri, flag, dm);
         }
         if ((smask & ~1u) == 0) {
             // the whole window lies in one stream

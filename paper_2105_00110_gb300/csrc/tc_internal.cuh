@@ -185,8 +185,12 @@ static const bool tc_dbg_registered = (dbg_register(&dbg_take_here), true);
 // that may be stale can only under-report set bits: an OR is issued only
 // when the word read lacks one of the bits, which skips the many repeated
 // settings of an edge that lies in several triangles.
+// Sets bits of a flag word: one atomic OR whose result is not used, so the
+// thread does not wait for it.  (Reading the word first to skip the atomic
+// when its bits are already set made every count slower: the read is a
+// dependent global load on the hot path.)
 __device__ __forceinline__ void flag_or(uint32_t* __restrict__ fb, int64_t word, uint32_t mask) {
-    if ((fb[word] & mask) != mask) atomicOr(&fb[word], mask);
+    atomicOr(&fb[word], mask);
 }
 __device__ __forceinline__ void flag_set(uint32_t* __restrict__ fb, int64_t p) {
     flag_or(fb, p >> 5, 1u << (p & 31));
