@@ -194,16 +194,22 @@ __device__ __forceinline__ void run_network_step(uint64_t* key, int len, int P, 
     }
 }
 
-// Runs up to kMidRun tails are sorted by one warp, longer ones by a CTA.
+// Runs up to kMidRun tails are sorted by one warp, longer ones by a CTA;
+// runs up to kMidShort tails by warps with a quarter of the shared memory,
+// so that more of them are resident (the run kernels wait mostly on their
+// loads, cursor atomics and stores).
 constexpr int kMidRun = 1024;
+constexpr int kMidShort = 256;
 
 // Runs of 1..32 tails.  A warp takes 32 rows at a time, one per lane:
 // single-tail rows are written at once, runs of 2..32 are sorted across the
 // warp's registers (keys in lanes 0..L-1, +inf above), kSmallGroup runs at
 // a time with the network sized to the longest of them.
-// Longer runs are queued: 33..kMidRun tails from the front of `big` for
-// k_runs_mid (count nbig[0]), more from its back for k_runs_big (count
-// nbig[1]); the two never meet, since there are at most n runs.
+// Longer runs are queued: 33..kMidShort tails from the front of `big`
+// (count nbig[0]) and kMidShort+1..kMidRun tails from the back of its first
+// n entries (count nbig[1]) for k_runs_mid, which never meet since there are
+// at most n runs; more than kMidRun tails after those n entries for
+// k_runs_big (count nbig[2], fewer than m / kMidRun).
 template <class C>
 __global__ void k_runs_small(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
                              const int64_t* __restrict__ hptr, const uint64_t* __restrict__ slot, int64_t n,
@@ -224,7 +230,8 @@ __global__ void k_runs_small(const int64_t* __restrict__ row_ptr, const int64_t*
                 re = row_ptr[r + 1];
             }
             if (L == 1) emit_tail(r, hs, re, slot[p0], hnext, col, head, edge_tail, core_t);
-            else if (L > kMidRun) big[n - 1 - (int64_t)atomicAdd(&nbig[1], 1u)] = (int32_t)r;
+            else if (L > kMidRun) big[n + (int64_t)atomicAdd(&nbig[2], 1u)] = (int32_t)r;
+            else if (L > kMidShort) big[n - 1 - (int64_t)atomicAdd(&nbig[1], 1u)] = (int32_t)r;
             else if (L > 32) big[atomicAdd(&nbig[0], 1u)] = (int32_t)r;
         }
         unsigned todo = __ballot_sync(0xffffffffu, L >= 2 && L <= 32);
@@ -277,23 +284,27 @@ __global__ void k_runs_small(const int64_t* __restrict__ row_ptr, const int64_t*
     }
 }
 
-// Queued runs of 33..kMidRun tails (nbig[0] of them, at the front of
-// `big`): one warp per run, the network in the warp's own shared region.
+// Queued runs of 33..kMidShort tails (CAP = kMidShort: nbig[0] of them at
+// the front of `big`) or kMidShort+1..kMidRun tails (CAP = kMidRun: nbig[1]
+// at the back of its first n entries): one warp per run, the network in the
+// warp's own shared region of CAP keys.
 constexpr int kMidWarps = 4;
 
-template <class C>
+template <class C, int CAP>
 __global__ void __launch_bounds__(32 * kMidWarps)
 k_runs_mid(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
            const int64_t* __restrict__ hptr, const uint64_t* __restrict__ slot, const int32_t* __restrict__ big,
-           const unsigned int* __restrict__ nbig, C* __restrict__ hnext, int32_t* __restrict__ col,
+           const unsigned int* __restrict__ nbig, int64_t n, C* __restrict__ hnext, int32_t* __restrict__ col,
            tc_head* __restrict__ head, int64_t* __restrict__ edge_tail, int64_t core_t) {
-    __shared__ uint64_t sk[kMidWarps][kMidRun];
+    static_assert(CAP == kMidShort || CAP == kMidRun, "one queue per capacity");
+    constexpr bool kBack = CAP == kMidRun;
+    __shared__ uint64_t sk[kMidWarps][CAP];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint64_t* key = sk[w];
-    const unsigned count = nbig[0];
+    const unsigned count = nbig[kBack ? 1 : 0];
     const unsigned warps = gridDim.x * kMidWarps;
     for (unsigned q = blockIdx.x * kMidWarps + w; q < count; q += warps) {
-        const int64_t r = big[q];
+        const int64_t r = kBack ? big[n - 1 - (int64_t)q] : big[q];
         const int64_t i0 = hptr[r];
         const int len = (int)(hptr[r + 1] - i0);
         for (int i = lane; i < len; i += 32) key[i] = slot[i0 + i];
@@ -311,9 +322,9 @@ k_runs_mid(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hsta
     }
 }
 
-// Queued runs longer than kMidRun (nbig[1] of them, at the back of `big`):
-// one CTA per run, the network in shared memory (up to kRunSmem keys) or in
-// place in `slot`.
+// Queued runs longer than kMidRun (nbig[2] of them, after the first n
+// entries of `big`): one CTA per run, the network in shared memory (up to
+// kRunSmem keys) or in place in `slot`.
 constexpr int kRunSmem = 4096;
 constexpr int kRunThreads = 512;
 
@@ -324,9 +335,9 @@ k_runs_big(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hsta
            const unsigned int* __restrict__ nbig, int64_t n, C* __restrict__ hnext, int32_t* __restrict__ col,
            tc_head* __restrict__ head, int64_t* __restrict__ edge_tail, int64_t core_t) {
     __shared__ uint64_t sk[kRunSmem];
-    const unsigned count = nbig[1];
+    const unsigned count = nbig[2];
     for (unsigned q = blockIdx.x; q < count; q += gridDim.x) {
-        const int64_t r = big[n - 1 - (int64_t)q];
+        const int64_t r = big[n + (int64_t)q];
         const int64_t i0 = hptr[r];
         const int len = (int)(hptr[r + 1] - i0);
         uint64_t* key = len <= kRunSmem ? sk : slot + i0;
@@ -502,8 +513,14 @@ tc_status build_runs(tc_graph* g, cudaStream_t s, int64_t m, int64_t n, int bits
     }
     {
         launch_scope ls("build_runs_mid", s);
-        k_runs_mid<<<sm_count() * 8, 32 * kMidWarps, 0, s>>>(g->row_ptr, g->hstart, hptr, slot, big, nbig, hnext,
-                                                             g->col, g->head, g->edge_tail, core_t);
+        k_runs_mid<C, kMidShort><<<sm_count() * 16, 32 * kMidWarps, 0, s>>>(
+            g->row_ptr, g->hstart, hptr, slot, big, nbig, n, hnext, g->col, g->head, g->edge_tail, core_t);
+        TC_LAUNCH_CHECK();
+    }
+    {
+        launch_scope ls("build_runs_long", s);
+        k_runs_mid<C, kMidRun><<<sm_count() * 8, 32 * kMidWarps, 0, s>>>(
+            g->row_ptr, g->hstart, hptr, slot, big, nbig, n, hnext, g->col, g->head, g->edge_tail, core_t);
         TC_LAUNCH_CHECK();
     }
     {
@@ -697,13 +714,13 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
         TC_TRY(sc.get(&keys, m));
         TC_TRY(sc.get(&slot, m));
         TC_TRY(sc.get(&dh, n + 1));
-        TC_TRY(sc.get(&big, n + 1));
-        TC_TRY(sc.get(&nbig, 2));
+        TC_TRY(sc.get(&big, n + m / kMidRun + 2));
+        TC_TRY(sc.get(&nbig, 3));
         TC_TRY(sc.get((uint8_t**)&hnext, (n + 1) * (narrow ? 4 : 8)));
         TC_TRY(sc.get((uint8_t**)&tnext, (n + 1) * (narrow ? 4 : 8)));
         TC_TRY(sc.get(&hptr, n + 1));
         TC_CUDA(cudaMemsetAsync(dh, 0, (n + 1) * 4, s));
-        TC_CUDA(cudaMemsetAsync(nbig, 0, 8, s));
+        TC_CUDA(cudaMemsetAsync(nbig, 0, 3 * sizeof(unsigned int), s));
         {
             launch_scope ls("build_edge_rank_keys", s);
             k_edge_rank_keys<<<grid_for(m), kThreads, 0, s>>>(g->edge_u, g->edge_v, rank, m, bits, keys, dh);

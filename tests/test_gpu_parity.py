@@ -279,7 +279,7 @@ def test_upload_timed_not_counted():
 @pytest.mark.parametrize("strategy", ["auto", "bitmap", "global"])
 def test_runs_of_every_length_closed_form(strategy):
     # K_k in rank space has a run of every length 0 .. k-1, so the build
-    # sorts runs on both sides of each tier boundary (32, 1024, and the
+    # sorts runs on both sides of each tier boundary (32, 256, 1024, and the
     # in-place sort above 4096); closed forms check every output
     k = 4200
     s, d, n = gg.complete_graph(k)

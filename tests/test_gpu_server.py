@@ -132,3 +132,33 @@ def test_free_with_waiting_requests_drops_them():
     for i in range(30):
         srv.submit(*gg.rmat(10, seed=i))
     srv.close()                                   # must return; running batch finishes
+
+
+def test_served_pool_requests_against_the_oracle():
+    # entries of the served workload's own request pool (its seed, both
+    # generator kinds, every decade of size up to 3·10^7 pairs), through a
+    # server set up as in the served workload, each against the whole oracle
+    # run on the host's threads
+    import os
+    specs = gg.served_pool_specs(256, 0x5EED0004, 1e3, 1e8)
+    pick = []
+    for lo, hi in ((1e3, 1e4), (1e4, 1e5), (1e5, 1e6), (1e6, 1e7), (1e7, 3e7)):
+        for kind in ("rmat", "grid"):
+            pick += [sp for sp in specs if sp["kind"] == kind and lo <= sp["pairs"] < hi][:2]
+    assert {sp["kind"] for sp in pick} == {"rmat", "grid"} and max(sp["pairs"] for sp in pick) >= 1e7
+    reqs = [gg.served_graph(sp) for sp in pick]
+    srv = tcg.Server(memory_budget_bytes=32 << 30, max_batch_pairs=1 << 25, workers=2)
+    try:
+        ids = [srv.submit(s, d, n) for s, d, n in reqs]
+        done = {r["id"]: r for r in srv.wait_all(600)}
+    finally:
+        srv.close()
+    assert sorted(done) == sorted(ids)
+    threads = os.cpu_count() or 1
+    for rid, (s, d, n) in zip(ids, reqs):
+        r = done[rid]
+        ref = oracle.run(s, d, n, "fast", threads=threads, algebraic=False)
+        assert r["status"] in (tcg.TC_OK, tcg.TC_NO_TRIANGLES)
+        assert r["triangles"] == ref["total"]
+        np.testing.assert_array_equal(bits(r["tri"]), bits(ref["tri"].astype(np.int64)))
+        np.testing.assert_array_equal(bits(r["tc"]), bits(ref["tc"]))
