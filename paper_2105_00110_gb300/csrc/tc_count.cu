@@ -372,6 +372,49 @@ __device__ __forceinline__ uint32_t octet_valid(int off, int len) {
 
 // The hit mask of one octet against a bitmap staging, with the hits counted
 // at their staged indices; the caller sets the octet's flags.
+// Staged index of the id at offset boff of a bitmap entry: the members
+// before the entry plus those below bit s = boff & 15 in it (bits [0, s)
+// shifted to the top by a clamped funnel shift, which gives 0 for s = 0).
+__device__ __forceinline__ int staged_index(uint32_t word, uint32_t boff) {
+    return (int)(word >> 16) + __popc(__funnelshift_lc(0u, word, 32u - (boff & 15u)));
+}
+
+// Ids of G consecutive octets inside their stream, bit 8 j + k for id k of
+// octet j: bits [max(0, -off), min(8 G, len - off)).
+template <int G>
+__device__ __forceinline__ uint32_t group_valid(int off, int len) {
+    static_assert(8 * G <= 32, "one 32-bit mask per group");
+    const int lo = off < 0 ? -off : 0;
+    const int hi = len - off < 8 * G ? len - off : 8 * G;
+    const uint32_t full = 8 * G == 32 ? 0xffffffffu : (1u << (8 * G)) - 1;
+    return hi > lo ? (full >> (8 * G - hi)) & (full << lo) : 0u;
+}
+
+// The hit mask of one octet against a bitmap staging (valid: the octet's
+// ids inside the stream), hits counted at their staged indices.
+__device__ __forceinline__ uint32_t octet_hits_masked(const lookup_bitmap& lk, const octet& o, uint32_t valid,
+                                                      uint32_t* cnt) {
+    uint32_t word[8], boff[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        boff[k] = min((uint32_t)(o.x[k] - lk.base), (uint32_t)lk.nbits);
+        word[k] = lk.bits[TC_IX(boff[k] >> 4, (lk.nbits >> 4) + 1)];
+    }
+    uint32_t hm = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        hm |= __funnelshift_l(word[k], word[k], (uint32_t)k - (boff[k] & 15u)) & (1u << k);
+    hm &= valid;
+    int l[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        l[k] = staged_index(word[k], boff[k]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if ((hm >> k) & 1u) atomicAdd(&cnt[TC_IX(l[k], lk.hv)], 1u);
+    return hm;
+}
+
 __device__ __forceinline__ uint32_t octet_hits_bitmap(const lookup_bitmap& lk, const octet& o, int off, int len,
                                                       uint32_t* cnt) {
     uint32_t word[8], boff[8];
@@ -393,11 +436,12 @@ __device__ __forceinline__ uint32_t octet_hits_bitmap(const lookup_bitmap& lk, c
         for (int k = 0; k < 8; ++k)
             hm |= (((word[k] >> (boff[k] & 15)) & 1u) & ((unsigned)(off + k) < (unsigned)len ? 1u : 0u)) << k;
     }
-    if (hm == 0) return 0;
+    // no early exit for an octet without hits: the branch costs more than
+    // the index arithmetic it would skip (almost every octet has a hit)
     int l[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-        l[k] = (hm >> k) & 1u ? (int)(word[k] >> 16) + __popc(word[k] & ((1u << (boff[k] & 15)) - 1)) : 0;
+        l[k] = staged_index(word[k], boff[k]);
 #pragma unroll
     for (int k = 0; k < 8; ++k)
         if ((hm >> k) & 1u) atomicAdd(&cnt[TC_IX(l[k], lk.hv)], 1u);
@@ -414,6 +458,9 @@ __device__ __forceinline__ uint32_t visit_octet_bitmap(const lookup_bitmap& lk, 
     return (uint32_t)__popc(hm);
 }
 
+#ifndef TC_GROUP_VALID
+#define TC_GROUP_VALID 1
+#endif
 // The G octets of a lane (8 G ids from the 8-aligned position pos) lie in at
 // most two 32-bit flag words when 8 G + 24 <= 64: their hit masks are put
 // side by side and each word gets one OR.
@@ -477,9 +524,15 @@ __device__ __forceinline__ uint32_t visit_group(const LK& lk, const octet (&o)[G
                                                 uint32_t* __restrict__ flag, const tc_dims& dm) {
     uint32_t h = 0;
     if constexpr (std::is_same<LK, lookup_bitmap>::value && CNT && !EC && TC_FLAG_COMBINE && G > 1) {
-        uint64_t hm = 0;
+        uint32_t hm = 0;
+        if (TC_GROUP_VALID) {
+            const uint32_t valid = group_valid<G>(off0, len);
 #pragma unroll
-        for (int j = 0; j < G; ++j) hm |= (uint64_t)octet_hits_bitmap(lk, o[j], off0 + 8 * j, len, cnt) << (8 * j);
+            for (int j = 0; j < G; ++j) hm |= octet_hits_masked(lk, o[j], (valid >> (8 * j)) & 0xffu, cnt) << (8 * j);
+        } else {
+#pragma unroll
+            for (int j = 0; j < G; ++j) hm |= octet_hits_bitmap(lk, o[j], off0 + 8 * j, len, cnt) << (8 * j);
+        }
         h = mark_group<G>(flag, pos, hm, dm);
     } else {
 #pragma unroll

@@ -56,12 +56,15 @@ struct __align__(16) tc_head {
 };
 
 // Planner parameters (tuned per batch by tc_batch_autotune).
+#ifndef TC_THREAD_WORK
+#define TC_THREAD_WORK 64
+#endif
 struct tc_plan_params {
     int64_t cta_min_work = 4096;   // W(v) at or above which v may become CTA items
     int64_t cta_chunk = 4194304;   // target wedges per CTA item (each chunk re-stages N_H(v));
                                    // the build sets it from the graph's wedges
     int64_t warp_chunk = 32768;    // target wedges per warp item
-    int64_t thread_work = 64;      // head entries + streamed ids at or below which a vertex
+    int64_t thread_work = TC_THREAD_WORK;   // head entries + streamed ids at or below which a vertex
                                    // with |N_H(v)| <= 32 is one thread's item (unions of many
                                    // graphs: 128, set by the build)
 };
