@@ -199,7 +199,10 @@ __device__ __forceinline__ void run_network_step(uint64_t* key, int len, int P, 
 // so that more of them are resident (the run kernels wait mostly on their
 // loads, cursor atomics and stores).
 constexpr int kMidRun = 1024;
-constexpr int kMidShort = 256;
+#ifndef TC_MID_SHORT
+#define TC_MID_SHORT 256
+#endif
+constexpr int kMidShort = TC_MID_SHORT;   // 256, or 512 with the register sort
 
 // Runs of 1..32 tails.  A warp takes 32 rows at a time, one per lane:
 // single-tail rows are written at once, runs of 2..32 are sorted across the
@@ -297,6 +300,7 @@ k_runs_mid(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hsta
            const unsigned int* __restrict__ nbig, int64_t n, C* __restrict__ hnext, int32_t* __restrict__ col,
            tc_head* __restrict__ head, int64_t* __restrict__ edge_tail, int64_t core_t) {
     static_assert(CAP == kMidShort || CAP == kMidRun, "one queue per capacity");
+    static_assert(kMidShort == 256 || kMidShort == 512, "register sort tiers: up to 16 keys a lane");
     constexpr bool kBack = CAP == kMidRun;
     __shared__ uint64_t sk[kMidWarps][CAP];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -319,6 +323,103 @@ k_runs_mid(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hsta
         const int64_t h = hstart[r], e = row_ptr[r + 1];
         for (int i = lane; i < len; i += 32) emit_tail(r, h + i, e, key[i], hnext, col, head, edge_tail, core_t);
         __syncwarp();
+    }
+}
+
+// Runs of 33..kMidShort tails sorted in registers instead (TC_RUNS_REG):
+// key i of the run (i = 32 e + lane, e < E) in register e of a lane, padded
+// with +inf to 32 E.  Compare-exchanges at distance j < 32 pair lanes
+// (shuffles), at j >= 32 pair registers of one lane; the mirror step of a
+// k-merge pairs i with i ^ (k - 1), i.e. lane ^ (k - 1) for k <= 32 and
+// register e ^ ((k - 1) >> 5) of lane ^ 31 above.  Loads and the emit's
+// col stores are coalesced (lane-consecutive), and no shared memory is used.
+#ifndef TC_RUNS_REG
+#define TC_RUNS_REG 1
+#endif
+template <int E>
+__device__ __forceinline__ void sort_run_regs(uint64_t (&x)[E], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32 * E; k <<= 1) {
+        if (k <= 32) {
+            const bool low = (lane & (k >> 1)) == 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const uint64_t y = shfl_xor64(x[e], k - 1);
+                x[e] = low ? (x[e] < y ? x[e] : y) : (x[e] < y ? y : x[e]);
+            }
+        } else {
+            // registers e (lower half of the k-block) and f = e ^ m pair with
+            // each other's values in lane ^ 31
+            const int m = (k - 1) >> 5;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int f = e ^ m;
+                if (e < f) {
+                    const uint64_t a = shfl_xor64(x[f], 31), b = shfl_xor64(x[e], 31);
+                    x[e] = x[e] < a ? x[e] : a;   // e has bit k/64 clear: the lower index
+                    x[f] = x[f] < b ? b : x[f];
+                }
+            }
+        }
+#pragma unroll
+        for (int j = k >> 2; j > 0; j >>= 1) {
+            if (j < 32) {
+                const bool low = (lane & j) == 0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const uint64_t y = shfl_xor64(x[e], j);
+                    x[e] = low ? (x[e] < y ? x[e] : y) : (x[e] < y ? y : x[e]);
+                }
+            } else {
+                const int je = j >> 5;
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if ((e & je) == 0) {
+                        const uint64_t a = x[e], b = x[e | je];
+                        x[e] = a < b ? a : b;
+                        x[e | je] = a < b ? b : a;
+                    }
+            }
+        }
+    }
+}
+
+template <class C, int E>
+__device__ __forceinline__ void run_regs(int lane, int64_t r, int64_t i0, int len, const uint64_t* __restrict__ slot,
+                                         int64_t h, int64_t end, C* __restrict__ hnext, int32_t* __restrict__ col,
+                                         tc_head* __restrict__ head, int64_t* __restrict__ edge_tail, int64_t core_t) {
+    uint64_t x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = 32 * e + lane;
+        x[e] = i < len ? slot[i0 + i] : ~0ull;
+    }
+    sort_run_regs<E>(x, lane);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = 32 * e + lane;
+        if (i < len) emit_tail(r, h + i, end, x[e], hnext, col, head, edge_tail, core_t);
+    }
+}
+
+template <class C>
+__global__ void __launch_bounds__(32 * kMidWarps)
+k_runs_mid_reg(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
+               const int64_t* __restrict__ hptr, const uint64_t* __restrict__ slot, const int32_t* __restrict__ big,
+               const unsigned int* __restrict__ nbig, C* __restrict__ hnext, int32_t* __restrict__ col,
+               tc_head* __restrict__ head, int64_t* __restrict__ edge_tail, int64_t core_t) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned count = nbig[0];
+    const unsigned warps = gridDim.x * kMidWarps;
+    for (unsigned q = blockIdx.x * kMidWarps + w; q < count; q += warps) {
+        const int64_t r = big[q];
+        const int64_t i0 = hptr[r];
+        const int len = (int)(hptr[r + 1] - i0);
+        const int64_t h = hstart[r], end = row_ptr[r + 1];
+        if (len <= 64) run_regs<C, 2>(lane, r, i0, len, slot, h, end, hnext, col, head, edge_tail, core_t);
+        else if (len <= 128) run_regs<C, 4>(lane, r, i0, len, slot, h, end, hnext, col, head, edge_tail, core_t);
+        else if (kMidShort <= 256 || len <= 256) run_regs<C, 8>(lane, r, i0, len, slot, h, end, hnext, col, head, edge_tail, core_t);
+        else run_regs<C, (kMidShort > 256 ? 16 : 8)>(lane, r, i0, len, slot, h, end, hnext, col, head, edge_tail, core_t);
     }
 }
 
@@ -513,8 +614,12 @@ tc_status build_runs(tc_graph* g, cudaStream_t s, int64_t m, int64_t n, int bits
     }
     {
         launch_scope ls("build_runs_mid", s);
-        k_runs_mid<C, kMidShort><<<sm_count() * 16, 32 * kMidWarps, 0, s>>>(
-            g->row_ptr, g->hstart, hptr, slot, big, nbig, n, hnext, g->col, g->head, g->edge_tail, core_t);
+        if (TC_RUNS_REG)
+            k_runs_mid_reg<C><<<sm_count() * 16, 32 * kMidWarps, 0, s>>>(
+                g->row_ptr, g->hstart, hptr, slot, big, nbig, hnext, g->col, g->head, g->edge_tail, core_t);
+        else
+            k_runs_mid<C, kMidShort><<<sm_count() * 16, 32 * kMidWarps, 0, s>>>(
+                g->row_ptr, g->hstart, hptr, slot, big, nbig, n, hnext, g->col, g->head, g->edge_tail, core_t);
         TC_LAUNCH_CHECK();
     }
     {

@@ -647,7 +647,7 @@ struct warp_smem {
     stream_table<32> tb;
 };
 #ifndef TC_WARP_FETCH
-#define TC_WARP_FETCH 2
+#define TC_WARP_FETCH 4
 #endif
 #ifndef TC_WARP_FILTER
 #define TC_WARP_FILTER 1
@@ -685,8 +685,11 @@ __device__ __forceinline__ int compact_warp(int lane, const entry& e, stream_tab
 constexpr int kWarpG = TC_WARP_G;   // octets (8 ids) per lane per window, warp items
 constexpr int kCtaG = TC_CTA_G;     // octets per lane per window, CTA items
 
+#ifndef TC_WARP_MIN_BLOCKS
+#define TC_WARP_MIN_BLOCKS 4
+#endif
 template <bool MERGE, bool EC>
-__global__ void __launch_bounds__(TC_CTA_THREADS, 4)
+__global__ void __launch_bounds__(TC_CTA_THREADS, TC_WARP_MIN_BLOCKS)
 k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
              const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
              const int32_t* __restrict__ it_v,

@@ -35,7 +35,9 @@
 
 #include "tc.h"
 
+#ifndef TC_WARP_CAP
 #define TC_WARP_CAP 512          // N_H(v) ids staged per warp item
+#endif
 #define TC_CTA_THREADS 256
 
 // Item classes of the count step.
