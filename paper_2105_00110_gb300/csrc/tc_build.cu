@@ -423,6 +423,126 @@ k_runs_mid_reg(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ 
     }
 }
 
+// Runs of kMidShort+1..kMidRun tails by one CTA of kMidWarps warps in
+// registers (TC_RUNS_CTA_REG): key i = 32 E w + 32 e + lane in register e of
+// lane `lane` of warp w, padded with +inf to 128 E.  Distances below 32 pair
+// lanes (shuffles), 32..32E-1 registers of one lane, 32E and above warps,
+// through one shared exchange of all keys per such step.
+#ifndef TC_RUNS_CTA_REG
+#define TC_RUNS_CTA_REG 1
+#endif
+template <int E>
+__device__ __forceinline__ void sort_run_cta(uint64_t (&x)[E], uint64_t* sx, int lane, int w) {
+    constexpr int P = 32 * E * kMidWarps;
+    const int me = 32 * E * w + lane;   // index of register 0
+#pragma unroll
+    for (int k = 2; k <= P; k <<= 1) {
+        if (k <= 32) {
+            const bool low = (lane & (k >> 1)) == 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const uint64_t y = shfl_xor64(x[e], k - 1);
+                x[e] = low ? (x[e] < y ? x[e] : y) : (x[e] < y ? y : x[e]);
+            }
+        } else if (k <= 32 * E) {
+            const int m = (k - 1) >> 5;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int f = e ^ m;
+                if (e < f) {
+                    const uint64_t a = shfl_xor64(x[f], 31), b = shfl_xor64(x[e], 31);
+                    x[e] = x[e] < a ? x[e] : a;
+                    x[f] = x[f] < b ? b : x[f];
+                }
+            }
+        } else {
+            // partner of i is i ^ (k - 1): another warp, register E-1-e, lane ^ 31
+#pragma unroll
+            for (int e = 0; e < E; ++e) sx[me + 32 * e] = x[e];
+            __syncthreads();
+            const int pw = w ^ ((k - 1) / (32 * E));
+            const bool low = (w & (k / (64 * E))) == 0;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const uint64_t y = sx[32 * E * pw + 32 * (E - 1 - e) + (lane ^ 31)];
+                x[e] = low ? (x[e] < y ? x[e] : y) : (x[e] < y ? y : x[e]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int j = k >> 2; j > 0; j >>= 1) {
+            if (j < 32) {
+                const bool low = (lane & j) == 0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const uint64_t y = shfl_xor64(x[e], j);
+                    x[e] = low ? (x[e] < y ? x[e] : y) : (x[e] < y ? y : x[e]);
+                }
+            } else if (j < 32 * E) {
+                const int je = j >> 5;
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if ((e & je) == 0) {
+                        const uint64_t a = x[e], b = x[e | je];
+                        x[e] = a < b ? a : b;
+                        x[e | je] = a < b ? b : a;
+                    }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) sx[me + 32 * e] = x[e];
+                __syncthreads();
+                const int pw = w ^ (j / (32 * E));
+                const bool low = (w & (j / (32 * E))) == 0;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const uint64_t y = sx[32 * E * pw + 32 * e + lane];
+                    x[e] = low ? (x[e] < y ? x[e] : y) : (x[e] < y ? y : x[e]);
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+template <class C, int E>
+__device__ __forceinline__ void run_cta(int lane, int w, uint64_t* sx, int64_t r, int64_t i0, int len,
+                                        const uint64_t* __restrict__ slot, int64_t h, int64_t end,
+                                        C* __restrict__ hnext, int32_t* __restrict__ col,
+                                        tc_head* __restrict__ head, int64_t* __restrict__ edge_tail, int64_t core_t) {
+    uint64_t x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = 32 * E * w + 32 * e + lane;
+        x[e] = i < len ? slot[i0 + i] : ~0ull;
+    }
+    sort_run_cta<E>(x, sx, lane, w);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = 32 * E * w + 32 * e + lane;
+        if (i < len) emit_tail(r, h + i, end, x[e], hnext, col, head, edge_tail, core_t);
+    }
+}
+
+template <class C>
+__global__ void __launch_bounds__(32 * kMidWarps)
+k_runs_long_cta(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
+                const int64_t* __restrict__ hptr, const uint64_t* __restrict__ slot, const int32_t* __restrict__ big,
+                const unsigned int* __restrict__ nbig, int64_t n, C* __restrict__ hnext, int32_t* __restrict__ col,
+                tc_head* __restrict__ head, int64_t* __restrict__ edge_tail, int64_t core_t) {
+    static_assert(32 * 8 * kMidWarps == kMidRun, "eight keys a thread cover the longest queued run");
+    __shared__ uint64_t sx[kMidRun];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned count = nbig[1];
+    for (unsigned q = blockIdx.x; q < count; q += gridDim.x) {
+        const int64_t r = big[n - 1 - (int64_t)q];
+        const int64_t i0 = hptr[r];
+        const int len = (int)(hptr[r + 1] - i0);
+        const int64_t h = hstart[r], end = row_ptr[r + 1];
+        if (len <= 512) run_cta<C, 4>(lane, w, sx, r, i0, len, slot, h, end, hnext, col, head, edge_tail, core_t);
+        else run_cta<C, 8>(lane, w, sx, r, i0, len, slot, h, end, hnext, col, head, edge_tail, core_t);
+    }
+}
+
 // Queued runs longer than kMidRun (nbig[2] of them, after the first n
 // entries of `big`): one CTA per run, the network in shared memory (up to
 // kRunSmem keys) or in place in `slot`.
@@ -624,8 +744,12 @@ tc_status build_runs(tc_graph* g, cudaStream_t s, int64_t m, int64_t n, int bits
     }
     {
         launch_scope ls("build_runs_long", s);
-        k_runs_mid<C, kMidRun><<<sm_count() * 8, 32 * kMidWarps, 0, s>>>(
-            g->row_ptr, g->hstart, hptr, slot, big, nbig, n, hnext, g->col, g->head, g->edge_tail, core_t);
+        if (TC_RUNS_CTA_REG)
+            k_runs_long_cta<C><<<sm_count() * 16, 32 * kMidWarps, 0, s>>>(
+                g->row_ptr, g->hstart, hptr, slot, big, nbig, n, hnext, g->col, g->head, g->edge_tail, core_t);
+        else
+            k_runs_mid<C, kMidRun><<<sm_count() * 8, 32 * kMidWarps, 0, s>>>(
+                g->row_ptr, g->hstart, hptr, slot, big, nbig, n, hnext, g->col, g->head, g->edge_tail, core_t);
         TC_LAUNCH_CHECK();
     }
     {
