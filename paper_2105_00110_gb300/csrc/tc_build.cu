@@ -93,41 +93,11 @@ __global__ void k_rank_apply(const uint64_t* __restrict__ sorted, int64_t n, int
     if (blockIdx.x == 0 && threadIdx.x == 0) degr[n] = 0;
 }
 
-// With TC_PLACE_ILP > 1 the rank-space re-keying and the tail placement
-// take that many edges a thread at once (strided by the grid), every load
-// (and, in the placement, every cursor atomic) issued before the stores.
-#ifndef TC_PLACE_ILP
-#define TC_PLACE_ILP 1
-#endif
-
 // Every undirected edge once in rank space: key (lo, hi) with lo < hi the
 // ranks of its ends, at its canonical id; d_H(lo) counted.
 __global__ void k_edge_rank_keys(const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
                                  const int32_t* __restrict__ rank, int64_t m, int bits,
                                  uint64_t* __restrict__ keys, int32_t* __restrict__ dh) {
-    if (TC_PLACE_ILP > 1) {   // U edges a thread: every rank read in flight at once
-        constexpr int U = TC_PLACE_ILP > 1 ? TC_PLACE_ILP : 1;
-        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < m; e0 += stride * U) {
-            uint64_t ru[U], rv[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int64_t e = e0 + u * stride;
-                ru[u] = e < m ? (uint64_t)rank[eu[e]] : 0;
-                rv[u] = e < m ? (uint64_t)rank[ev[e]] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int64_t e = e0 + u * stride;
-                if (e < m) {
-                    const uint64_t lo = ru[u] < rv[u] ? ru[u] : rv[u], hi = ru[u] < rv[u] ? rv[u] : ru[u];
-                    keys[e] = (lo << bits) | hi;
-                    atomicAdd(&dh[lo], 1);
-                }
-            }
-        }
-        return;
-    }
     GRID_STRIDE(e, m) {
         const uint64_t ru = (uint64_t)rank[eu[e]], rv = (uint64_t)rank[ev[e]];
         const uint64_t lo = ru < rv ? ru : rv, hi = ru < rv ? rv : ru;
@@ -157,23 +127,6 @@ template <class C>
 __global__ void k_tail_place(const uint64_t* __restrict__ keys, int64_t m, int bits, C* __restrict__ tnext,
                              uint64_t* __restrict__ slot) {
     const uint64_t mask = (1ull << bits) - 1;
-    if (TC_PLACE_ILP > 1) {
-        constexpr int U = TC_PLACE_ILP > 1 ? TC_PLACE_ILP : 1;
-        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < m; e0 += stride * U) {
-            uint64_t k[U];
-            int64_t i[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) k[u] = e0 + u * stride < m ? keys[e0 + u * stride] : 0;
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (e0 + u * stride < m) i[u] = (int64_t)atomicAdd(&tnext[k[u] >> bits], (C)1);
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (e0 + u * stride < m) slot[i[u]] = ((k[u] & mask) << 32) | (uint64_t)(e0 + u * stride);
-        }
-        return;
-    }
     GRID_STRIDE(e, m) {
         const uint64_t k = keys[e];
         const uint64_t lo = k >> bits, hi = k & mask;
