@@ -692,7 +692,7 @@ template <bool MERGE, bool EC>
 __global__ void __launch_bounds__(TC_CTA_THREADS, TC_WARP_MIN_BLOCKS)
 k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
              const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
-             const int32_t* __restrict__ it_v,
+             const tc_item* __restrict__ it_d, const int32_t* __restrict__ it_nb,
              const int64_t* __restrict__ it_pb, const int64_t* __restrict__ it_pe,
              int64_t n_items, int64_t it_off, int64_t it_stride, ull* __restrict__ cursor, int strategy,
              ull* __restrict__ tri, uint32_t* __restrict__ flag, ull* __restrict__ total, tc_dims dm) {
@@ -710,12 +710,12 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
         const int64_t lim = min(base + kWarpItemsPerFetch, n_items);
         for (int64_t it = base; it < lim; ++it) {
             const int64_t gi = it_off + it_stride * it;   // this shard's it-th item
-            const int32_t v = it_v[gi];
+            const tc_item d = it_d[gi];
+            const int32_t v = d.v, nbits = it_nb[gi];
             const int64_t pb = it_pb[gi], pe = it_pe[gi];
             entry nxt = fetch_entry(pb + lane, pe, head, dm);
-            const int64_t h0 = hstart[TC_IX(v, dm.n)], h1 = row_ptr[TC_IX(v, dm.n) + 1];
-            const int hv = (int)(h1 - h0);
-            const int32_t nbits = col[TC_IX(h1 - 1, dm.e2)] - v;
+            const int64_t h0 = d.h0;
+            const int hv = d.hv;
             const bool use_bitmap = allow_bitmap && warp_bitmap_fits((nbits + 31) >> 5, hv);
             // the filter in front of the bisection: automatic strategy only,
             // so that a forced binary search still bisects every id
@@ -786,7 +786,7 @@ template <int LOOK, bool MERGE, bool EC>
 __global__ void __launch_bounds__(kCtaT, TC_CTA_MIN_BLOCKS)
 k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
             const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
-            const int32_t* __restrict__ it_v,
+            const tc_item* __restrict__ it_d, const int32_t* __restrict__ it_nb,
             const int64_t* __restrict__ it_pb, const int64_t* __restrict__ it_pe,
             int64_t n_items, int64_t it_off, int64_t it_stride, ull* __restrict__ cursor, int strategy,
             ull* __restrict__ tri,
@@ -807,18 +807,18 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         const int64_t it = s_item;
         if (it >= n_items) break;
         const int64_t gi = it_off + it_stride * it;   // this shard's it-th item
-        const int32_t v = it_v[gi];
+        const tc_item d = it_d[gi];
+        const int32_t v = d.v;
         const int64_t pb = it_pb[gi], pe = it_pe[gi];
         entry nxt = fetch_entry(pb + t, pe, head, dm);
-        const int64_t h0 = hstart[TC_IX(v, dm.n)], h1 = row_ptr[TC_IX(v, dm.n) + 1];
-        const int hv = (int)(h1 - h0);
+        const int64_t h0 = d.h0;
+        const int hv = d.hv;
         uint32_t* cnt = nullptr;
         lookup_bitmap lb{};
         lookup_sorted ls{};
         lookup_global lg{};
         if (LOOK == L_BITMAP) {
-            lb = build_bitmap(t, nt, dyn, v, h0, hv, col[TC_IX(h1 - 1, dm.e2)] - v, col, cnt, cbar, s_scan, lane, warp,
-                              kCtaItemWarps, dm);
+            lb = build_bitmap(t, nt, dyn, v, h0, hv, it_nb[gi], col, cnt, cbar, s_scan, lane, warp, kCtaItemWarps, dm);
         } else if (LOOK == L_SORTED) {
             int32_t* ids = (int32_t*)dyn;
             cnt = (uint32_t*)(ids + hv);
@@ -927,7 +927,7 @@ template <bool EC>
 __global__ void __launch_bounds__(kThreadBlock)
 k_count_thread(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
-               const int32_t* __restrict__ it_v, const int64_t* __restrict__ it_pb,
+               const tc_item* __restrict__ it_d, const int32_t* __restrict__ it_nb, const int64_t* __restrict__ it_pb,
                const int64_t* __restrict__ it_pe, int64_t n_items, int64_t it_off, int64_t it_stride,
                ull* __restrict__ cursor, int strategy,
                ull* __restrict__ tri, uint32_t* __restrict__ flag, ull* __restrict__ total, tc_dims dm) {
@@ -936,9 +936,10 @@ k_count_thread(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ 
     ull tv_all = 0;
     for (int64_t it = blockIdx.x * (int64_t)blockDim.x + t; it < n_items; it += (int64_t)gridDim.x * blockDim.x) {
         const int64_t gi = it_off + it_stride * it;   // this shard's it-th item
-        const int32_t v = it_v[gi];
-        const int64_t h0 = hstart[TC_IX(v, dm.n)], h1 = row_ptr[TC_IX(v, dm.n) + 1];
-        const int hv = (int)(h1 - h0);
+        const tc_item d = it_d[gi];
+        const int32_t v = d.v;
+        const int64_t h0 = d.h0;
+        const int hv = d.hv;
         // loads issued kThreadILP at a time, so that one thread's chain of
         // small reads does not wait for each in turn
         for (int k0 = 0; k0 < hv; k0 += kThreadILP) {
@@ -1086,12 +1087,14 @@ __global__ void k_classify(const int64_t* __restrict__ row_ptr, const int64_t* _
 }
 
 struct emit_targets {
-    int32_t* v[TC_NUM_CLS];
+    tc_item* d[TC_NUM_CLS];
+    int32_t* nb[TC_NUM_CLS];
     int64_t* pb[TC_NUM_CLS];
     int64_t* pe[TC_NUM_CLS];
 };
 
 __global__ void k_emit(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hstart,
+                       const int32_t* __restrict__ col,
                        int64_t n, const int8_t* __restrict__ cls, const int64_t* __restrict__ cnt,
                        const int64_t* __restrict__ off, emit_targets tg) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -1099,13 +1102,17 @@ __global__ void k_emit(const int64_t* __restrict__ row_ptr, const int64_t* __res
         const int c = cls[i];
         if (c < 0) continue;
         const int64_t r = n - 1 - i;
-        const int64_t b = row_ptr[r], lv = hstart[r] - b;
+        const int64_t b = row_ptr[r], h0 = hstart[r], lv = h0 - b, h1 = row_ptr[r + 1];
         const int64_t k = cnt[c * (n + 1) + i], o = off[c * (n + 1) + i];
-        int32_t* vv = tg.v[c];
+        const tc_item d{h0, (int32_t)r, (int32_t)(h1 - h0)};
+        const int32_t nbits = h1 > h0 ? col[h1 - 1] - (int32_t)r : 0;
+        tc_item* dd = tg.d[c];
+        int32_t* nbb = tg.nb[c];
         int64_t* pbb = tg.pb[c];
         int64_t* pee = tg.pe[c];
         for (int64_t j = 0; j < k; ++j) {
-            vv[o + j] = (int32_t)r;
+            dd[o + j] = d;
+            nbb[o + j] = nbits;
             pbb[o + j] = b + lv * j / k;
             pee[o + j] = b + lv * (j + 1) / k;
         }
@@ -1174,7 +1181,7 @@ tc_status launch_persistent(K kernel, const char* name, size_t smem, int64_t all
     int64_t blocks = std::min<int64_t>((int64_t)sm_count() * per_sm, items);
     launch_scope ls(name, s);
     kernel<<<(int)blocks, threads, smem, s>>>(g->row_ptr, g->col, g->hstart, g->head,
-                                                     p.v[c], p.pb[c], p.pe[c], items, (int64_t)shard,
+                                                     p.d[c], p.nb[c], p.pb[c], p.pe[c], items, (int64_t)shard,
                                                      (int64_t)num_shards, cursor,
                                                      g->strategy, g->tri, marks, g->counters, dims_of(g));
     TC_LAUNCH_CHECK();
@@ -1185,10 +1192,12 @@ tc_status launch_persistent(K kernel, const char* name, size_t smem, int64_t all
 
 void free_plan(tc_plan& p, cudaStream_t s) {
     for (int c = 0; c < TC_NUM_CLS; ++c) {
-        dfree(p.v[c], s);
+        dfree(p.d[c], s);
+        dfree(p.nb[c], s);
         dfree(p.pb[c], s);
         dfree(p.pe[c], s);
-        p.v[c] = nullptr;
+        p.d[c] = nullptr;
+        p.nb[c] = nullptr;
         p.pb[c] = p.pe[c] = nullptr;
         p.count[c] = 0;
     }
@@ -1250,7 +1259,8 @@ tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s) {
     PLAN_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < TC_NUM_CLS; ++c) {
         p.count[c] = (int64_t)h.items[c];
-        PLAN_TRY(dalloc((void**)&p.v[c], (p.count[c] + 1) * 4, s));
+        PLAN_TRY(dalloc((void**)&p.d[c], (p.count[c] + 1) * sizeof(tc_item), s));
+        PLAN_TRY(dalloc((void**)&p.nb[c], (p.count[c] + 1) * 4, s));
         PLAN_TRY(dalloc((void**)&p.pb[c], (p.count[c] + 1) * 8, s));
         PLAN_TRY(dalloc((void**)&p.pe[c], (p.count[c] + 1) * 8, s));
     }
@@ -1258,11 +1268,12 @@ tc_status make_plan(tc_graph* g, int strategy, cudaStream_t s) {
         launch_scope ls("plan_emit", s);
         emit_targets tg;
         for (int c = 0; c < TC_NUM_CLS; ++c) {
-            tg.v[c] = p.v[c];
+            tg.d[c] = p.d[c];
+            tg.nb[c] = p.nb[c];
             tg.pb[c] = p.pb[c];
             tg.pe[c] = p.pe[c];
         }
-        k_emit<<<blocks_for(n), 256, 0, s>>>(g->row_ptr, g->hstart, n, cls, cnt, off, tg);
+        k_emit<<<blocks_for(n), 256, 0, s>>>(g->row_ptr, g->hstart, g->col, n, cls, cnt, off, tg);
         PLAN_CUDA(cudaGetLastError());
     }
     p.smem[TC_CLS_BITMAP_S] = kBitmapSmallSmem;

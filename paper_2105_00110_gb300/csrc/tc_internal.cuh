@@ -71,10 +71,20 @@ struct tc_plan_params {
                                    // graphs: 128, set by the build)
 };
 
+// What a count kernel needs of an item's middle vertex v, in one 16-byte
+// load: where N_H(v) starts in the CSR and how long it is (so that staging
+// does not wait on two dependent loads of row_ptr and hstart first).
+struct tc_item {
+    int64_t h0;    // hstart[v]
+    int32_t v;
+    int32_t hv;    // |N_H(v)|
+};
+
 struct tc_plan {
     int strategy = -1;                 // strategy the plan was made for
     int64_t count[TC_NUM_CLS] = {};
-    int32_t* v[TC_NUM_CLS] = {};       // middle vertex of each item
+    tc_item* d[TC_NUM_CLS] = {};       // middle vertex of each item
+    int32_t* nb[TC_NUM_CLS] = {};      // its id window max N_H(v) - v (0 if N_H(v) is empty)
     int64_t* pb[TC_NUM_CLS] = {};      // head-entry range [pb, pe) of the item
     int64_t* pe[TC_NUM_CLS] = {};
     size_t smem[TC_NUM_CLS] = {};      // dynamic shared memory of the class's kernel
