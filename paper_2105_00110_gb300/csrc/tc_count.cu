@@ -57,6 +57,11 @@ constexpr int kCtaWarps = TC_CTA_THREADS / 32;
 #endif
 constexpr int kCtaT = TC_CTA_ITEM_THREADS;
 constexpr int kCtaItemWarps = kCtaT / 32;
+// CTA chunk target below which the small-bitmap class runs 2 kCtaT threads
+#ifndef TC_WIDE_CTA_CHUNK
+#define TC_WIDE_CTA_CHUNK (1 << 17)
+#endif
+constexpr int64_t kWideCtaChunk = TC_WIDE_CTA_CHUNK;
 #ifndef TC_CTA_MIN_BLOCKS
 #define TC_CTA_MIN_BLOCKS (1024 / TC_CTA_ITEM_THREADS)   // CTAs per SM the CTA-item kernels are compiled for
 #endif
@@ -778,12 +783,14 @@ k_count_warp(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ co
 }
 
 // ------------------------------------------------------------- CTA items
-// One CTA per item; the 8 warps share the staged N_H(v).  The item's head
-// entries are taken in rounds of 256 (a stream table, the next round's
-// entries loaded while this one streams); the round's units are split
-// evenly over the warps.
-template <int LOOK, bool MERGE, bool EC>
-__global__ void __launch_bounds__(kCtaT, TC_CTA_MIN_BLOCKS)
+// One CTA of T threads per item; its T / 32 warps share the staged N_H(v).
+// The item's head entries are taken in rounds of T (a stream table, the next
+// round's entries loaded while this one streams); the round's units are
+// split evenly over the warps.  T = 256 by default; graphs whose CTA items
+// are small (a small chunk target, e.g. grids with Chung-Lu hubs) take
+// T = 512, so that staging and each round are shared by twice the warps.
+template <int LOOK, bool MERGE, bool EC, int T = kCtaT>
+__global__ void __launch_bounds__(T, 1024 / T)
 k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
             const int64_t* __restrict__ hstart, const tc_head* __restrict__ head,
             const tc_item* __restrict__ it_d, const int32_t* __restrict__ it_nb,
@@ -792,13 +799,13 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             ull* __restrict__ tri,
             uint32_t* __restrict__ flag, ull* __restrict__ total, tc_dims dm) {
     extern __shared__ __align__(16) uint8_t dyn[];
-    __shared__ __align__(16) stream_table<kCtaT> tb;
+    __shared__ __align__(16) stream_table<T> tb;
     __shared__ int64_t s_item;
-    __shared__ ull s_tv[kCtaItemWarps];
-    __shared__ uint32_t s_scan[kCtaItemWarps];
-    __shared__ int s_cnt[kCtaItemWarps];
+    __shared__ ull s_tv[(T / 32)];
+    __shared__ uint32_t s_scan[(T / 32)];
+    __shared__ int s_cnt[(T / 32)];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int t = threadIdx.x, nt = kCtaT;
+    const int t = threadIdx.x, nt = T;
     auto cbar = [] { __syncthreads(); };
     for (;;) {
         __syncthreads();
@@ -818,7 +825,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         lookup_sorted ls{};
         lookup_global lg{};
         if (LOOK == L_BITMAP) {
-            lb = build_bitmap(t, nt, dyn, v, h0, hv, it_nb[gi], col, cnt, cbar, s_scan, lane, warp, kCtaItemWarps, dm);
+            lb = build_bitmap(t, nt, dyn, v, h0, hv, it_nb[gi], col, cnt, cbar, s_scan, lane, warp, (T / 32), dm);
         } else if (LOOK == L_SORTED) {
             int32_t* ids = (int32_t*)dyn;
             cnt = (uint32_t*)(ids + hv);
@@ -832,9 +839,9 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             lg = lookup_global{col + h0, hv};
         }
         ull tv = 0;
-        for (int64_t r0 = pb; r0 < pe; r0 += kCtaT) {
+        for (int64_t r0 = pb; r0 < pe; r0 += T) {
             const entry cur = nxt;
-            nxt = fetch_entry(r0 + kCtaT + t, pe, head, dm);   // in flight meanwhile
+            nxt = fetch_entry(r0 + T + t, pe, head, dm);   // in flight meanwhile
             // compact the round's non-empty streams: warp scans of the group
             // counts, then the warp totals
             const int ng = entry_groups<kCtaG>(cur);
@@ -852,7 +859,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             __syncthreads();
             int before_g = 0, before_c = 0, GT = 0, NC = 0;
 #pragma unroll
-            for (int k = 0; k < kCtaItemWarps; ++k) {
+            for (int k = 0; k < (T / 32); ++k) {
                 const int sg = (int)s_scan[k], sc = s_cnt[k];
                 before_g += k < warp ? sg : 0;
                 before_c += k < warp ? sc : 0;
@@ -862,21 +869,21 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
             if (ng > 0) put_stream(cur, before_c + __popc(nz & ((1u << lane) - 1)), before_g + incl - ng, tb);
             __syncthreads();
             if (MERGE) {
-                merge_streams<kCtaT, EC>(lane, (NC * warp) / kCtaItemWarps, (NC * (warp + 1)) / kCtaItemWarps, tb, ls.ids, hv, cnt, col, flag, dm);
+                merge_streams<T, EC>(lane, (NC * warp) / (T / 32), (NC * (warp + 1)) / (T / 32), tb, ls.ids, hv, cnt, col, flag, dm);
             } else {
-                const int gb = (int)(((int64_t)GT * warp) / kCtaItemWarps), ge = (int)(((int64_t)GT * (warp + 1)) / kCtaItemWarps);
+                const int gb = (int)(((int64_t)GT * warp) / (T / 32)), ge = (int)(((int64_t)GT * (warp + 1)) / (T / 32));
                 if (LOOK == L_BITMAP)
-                    walk_groups<lookup_bitmap, true, kCtaT, kCtaG, EC>(lane, tb, NC, gb, ge, lb, cnt, h0, col, tri, flag, dm);
+                    walk_groups<lookup_bitmap, true, T, kCtaG, EC>(lane, tb, NC, gb, ge, lb, cnt, h0, col, tri, flag, dm);
                 else if (LOOK == L_SORTED)
-                    walk_groups<lookup_sorted, true, kCtaT, kCtaG, EC>(lane, tb, NC, gb, ge, ls, cnt, h0, col, tri, flag, dm);
+                    walk_groups<lookup_sorted, true, T, kCtaG, EC>(lane, tb, NC, gb, ge, ls, cnt, h0, col, tri, flag, dm);
                 else
-                    walk_groups<lookup_global, false, kCtaT, kCtaG, EC>(lane, tb, NC, gb, ge, lg, nullptr, h0, col, tri, flag, dm);
+                    walk_groups<lookup_global, false, T, kCtaG, EC>(lane, tb, NC, gb, ge, lg, nullptr, h0, col, tri, flag, dm);
             }
             __syncthreads();   // every group of the round is done
             // no barrier after the closes: the next round rewrites the table
             // only after its first barrier, which every thread reaches once
             // its own close is done
-            if (t < NC) close_stream<kCtaT, EC>(t, tb, tri, flag, tv, dm);
+            if (t < NC) close_stream<T, EC>(t, tb, tri, flag, tv, dm);
         }
         tv = warp_sum(tv);
         if (lane == 0) s_tv[warp] = tv;
@@ -892,7 +899,7 @@ k_count_cta(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col
         }
         if (t == 0) {
             ull sum = 0;
-            for (int k = 0; k < kCtaItemWarps; ++k) sum += s_tv[k];
+            for (int k = 0; k < (T / 32); ++k) sum += s_tv[k];
             if (sum) {
                 atomicAdd(&tri[TC_IX(v, dm.n)], sum);
                 atomicAdd(total, sum);
@@ -1328,9 +1335,18 @@ tc_status launch_count_kernels(tc_graph* g, cudaStream_t s, uint32_t* marks, int
     TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC>, nm[0], p.smem[TC_CLS_BITMAP_L],
                              p.count[TC_CLS_BITMAP_L], s, g, p, TC_CLS_BITMAP_L, cur + TC_CLS_BITMAP_L, marks,
                              shard, num_shards, kCtaT));
-    TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC>, nm[1], p.smem[TC_CLS_BITMAP_S],
-                             p.count[TC_CLS_BITMAP_S], s, g, p, TC_CLS_BITMAP_S, cur + TC_CLS_BITMAP_S, marks,
-                             shard, num_shards, kCtaT));
+    // small CTA items (grids with Chung-Lu hubs: 2^16-wedge chunks) share
+    // their staging and rounds over 16 warps (the 4096^2 grid's bitmap
+    // kernel 2.17 -> 1.47 ms); R-MAT's larger items keep 8 (16 were 20 %
+    // slower at scale 22, chunks of 2^18.8 wedges, and 8 % at scale 24)
+    if (g->params.cta_chunk < kWideCtaChunk)
+        TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC, 2 * kCtaT>, nm[1], p.smem[TC_CLS_BITMAP_S],
+                                 p.count[TC_CLS_BITMAP_S], s, g, p, TC_CLS_BITMAP_S, cur + TC_CLS_BITMAP_S, marks,
+                                 shard, num_shards, 2 * kCtaT));
+    else
+        TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC>, nm[1], p.smem[TC_CLS_BITMAP_S],
+                                 p.count[TC_CLS_BITMAP_S], s, g, p, TC_CLS_BITMAP_S, cur + TC_CLS_BITMAP_S, marks,
+                                 shard, num_shards, kCtaT));
     if (p.count[TC_CLS_CTA_LIST] > 0) {
         // lists longer than the shared budget are searched in place
         const bool fits = g->strategy != TC_STRATEGY_GLOBAL &&
