@@ -62,6 +62,12 @@ constexpr int kCtaItemWarps = kCtaT / 32;
 #define TC_WIDE_CTA_CHUNK (1 << 17)
 #endif
 constexpr int64_t kWideCtaChunk = TC_WIDE_CTA_CHUNK;
+// The large-bitmap class (100 KB of shared memory, two CTAs per SM) runs
+// 16-warp CTAs, so that an SM holds 32 warps instead of 16 (R-MAT scale
+// 24: 2.22 -> 2.14 ms)
+#ifndef TC_WIDE_L
+#define TC_WIDE_L 1
+#endif
 #ifndef TC_CTA_MIN_BLOCKS
 #define TC_CTA_MIN_BLOCKS (1024 / TC_CTA_ITEM_THREADS)   // CTAs per SM the CTA-item kernels are compiled for
 #endif
@@ -1332,9 +1338,14 @@ tc_status launch_count_kernels(tc_graph* g, cudaStream_t s, uint32_t* marks, int
                              p.count[TC_CLS_THREAD], s, g, p, TC_CLS_THREAD, cur + TC_CLS_THREAD, marks, shard,
                              num_shards, kThreadBlock));
     // heaviest classes first; each kernel drains its own item queue
-    TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC>, nm[0], p.smem[TC_CLS_BITMAP_L],
-                             p.count[TC_CLS_BITMAP_L], s, g, p, TC_CLS_BITMAP_L, cur + TC_CLS_BITMAP_L, marks,
-                             shard, num_shards, kCtaT));
+    if (TC_WIDE_L)
+        TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC, 2 * kCtaT>, nm[0], p.smem[TC_CLS_BITMAP_L],
+                                 p.count[TC_CLS_BITMAP_L], s, g, p, TC_CLS_BITMAP_L, cur + TC_CLS_BITMAP_L, marks,
+                                 shard, num_shards, 2 * kCtaT));
+    else
+        TC_TRY(launch_persistent(k_count_cta<L_BITMAP, false, EC>, nm[0], p.smem[TC_CLS_BITMAP_L],
+                                 p.count[TC_CLS_BITMAP_L], s, g, p, TC_CLS_BITMAP_L, cur + TC_CLS_BITMAP_L, marks,
+                                 shard, num_shards, kCtaT));
     // small CTA items (grids with Chung-Lu hubs: 2^16-wedge chunks) share
     // their staging and rounds over 16 warps (the 4096^2 grid's bitmap
     // kernel 2.17 -> 1.47 ms); R-MAT's larger items keep 8 (16 were 20 %
