@@ -194,15 +194,15 @@ __device__ __forceinline__ void run_network_step(uint64_t* key, int len, int P, 
     }
 }
 
-// Runs up to kMidRun tails are sorted by one warp, longer ones by a CTA;
-// runs up to kMidShort tails by warps with a quarter of the shared memory,
-// so that more of them are resident (the run kernels wait mostly on their
-// loads, cursor atomics and stores).
+// Runs of 33..kMidShort tails are sorted by one warp, kMidShort+1..kMidRun
+// by one CTA of kMidWarps warps, longer ones by a CTA in shared memory (or
+// in place); the first two in registers (below), with the shared-memory
+// networks of k_runs_mid kept as the alternative.
 constexpr int kMidRun = 1024;
 #ifndef TC_MID_SHORT
 #define TC_MID_SHORT 256
 #endif
-constexpr int kMidShort = TC_MID_SHORT;   // 256, or 512 with the register sort
+constexpr int kMidShort = TC_MID_SHORT;   // longest run of the one-warp tier (512 spilled: slower)
 
 // Runs of 1..32 tails.  A warp takes 32 rows at a time, one per lane:
 // single-tail rows are written at once, runs of 2..32 are sorted across the
