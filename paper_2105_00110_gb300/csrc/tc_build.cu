@@ -600,6 +600,10 @@ struct row_stats {
 // streams for middle vertex v, plus shape statistics.  Rows ascend in
 // degree: rows below band[0] (degree <= 32) take one thread each, the rest
 // one warp each.
+// Rows of degree above 4096 get one CTA each in the per-row work (below).
+#ifndef TC_ROW_WORK_CTA
+#define TC_ROW_WORK_CTA 1
+#endif
 struct row_acc {
     unsigned long long h2 = 0, w = 0, dh = 0, maxh = 0, maxd = 0;
     __device__ __forceinline__ void add(unsigned long long hv, unsigned long long d, unsigned long long wr) {
@@ -656,7 +660,8 @@ __global__ void k_row_work_warp(const int64_t* __restrict__ row_ptr, const int64
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     row_acc acc;
-    for (int64_t r = band[0] + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); r < n; r += warps) {
+    const int64_t r1 = TC_ROW_WORK_CTA ? band[1] : n;   // rows above degree 4096: k_row_work_cta
+    for (int64_t r = band[0] + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); r < r1; r += warps) {
         const int64_t b = row_ptr[r], h = hstart[r], e = row_ptr[r + 1];
         unsigned long long w = 0;
         for (int64_t p = b + lane; p < h; p += 32) w += (unsigned long long)head[p].hrem;
@@ -665,6 +670,35 @@ __global__ void k_row_work_warp(const int64_t* __restrict__ row_ptr, const int64
             work[r] = (int64_t)w;
             acc.add((unsigned long long)(e - h), (unsigned long long)(e - b), w);
         }
+    }
+    acc.flush(st);
+}
+
+// Rows of degree above 4096 (ranks band[1] .. n - 1, the hubs, up to
+// hundreds of thousands of head entries each): one CTA per row, so that
+// the last hub rows do not each keep a single warp busy after the rest.
+__global__ void __launch_bounds__(512) k_row_work_cta(const int64_t* __restrict__ row_ptr,
+                                                      const int64_t* __restrict__ hstart,
+                                                      const tc_head* __restrict__ head,
+                                                      const int64_t* __restrict__ band, int64_t n,
+                                                      int64_t* __restrict__ work, row_stats* __restrict__ st) {
+    __shared__ unsigned long long part[16];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    row_acc acc;
+    for (int64_t r = band[1] + blockIdx.x; r < n; r += gridDim.x) {
+        const int64_t b = row_ptr[r], h = hstart[r], e = row_ptr[r + 1];
+        unsigned long long w = 0;
+        for (int64_t p = b + threadIdx.x; p < h; p += blockDim.x) w += (unsigned long long)head[p].hrem;
+        for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (lane == 0) part[wp] = w;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long s = 0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += part[k];
+            work[r] = (int64_t)s;
+            acc.add((unsigned long long)(e - h), (unsigned long long)(e - b), s);
+        }
+        __syncthreads();
     }
     acc.flush(st);
 }
@@ -1008,6 +1042,12 @@ tc_status build_graph(tc_graph* g, const void* src, const void* dst, int64_t np,
             const int bw = (int)std::min<int64_t>((n * 32 + kThreads - 1) / kThreads, (int64_t)cap);
             k_row_work_warp<<<std::max(bw, 1), kThreads, 0, s>>>(g->row_ptr, g->hstart, g->head, d_band, n,
                                                                  g->work, dst_stats);
+            TC_LAUNCH_CHECK();
+        }
+        if (TC_ROW_WORK_CTA) {
+            launch_scope ls("build_row_work_cta", s);
+            k_row_work_cta<<<sm_count() * 4, 512, 0, s>>>(g->row_ptr, g->hstart, g->head, d_band, n, g->work,
+                                                          dst_stats);
             TC_LAUNCH_CHECK();
         }
     }
