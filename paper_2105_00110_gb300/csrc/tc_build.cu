@@ -578,9 +578,14 @@ k_runs_big(const int64_t* __restrict__ row_ptr, const int64_t* __restrict__ hsta
     }
 }
 
-// First ranks whose degree exceeds 32 and 4096 (degrees ascend with rank).
+// First ranks whose degree exceeds 32 and TC_BAND_CTA (degrees ascend with
+// rank): the gather and the per-row work take one thread, one warp and one
+// CTA per row in the three bands.
+#ifndef TC_BAND_CTA
+#define TC_BAND_CTA 4096
+#endif
 __global__ void k_bands(const int64_t* __restrict__ row_ptr, int64_t n, int64_t* __restrict__ band) {
-    const int64_t lim[2] = {32, 4096};
+    const int64_t lim[2] = {32, TC_BAND_CTA};
     for (int k = 0; k < 2; ++k) {
         int64_t lo = 0, hi = n;
         while (lo < hi) {
