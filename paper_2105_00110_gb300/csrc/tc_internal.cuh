@@ -88,6 +88,7 @@ struct tc_plan {
     int64_t* pb[TC_NUM_CLS] = {};      // head-entry range [pb, pe) of the item
     int64_t* pe[TC_NUM_CLS] = {};
     size_t smem[TC_NUM_CLS] = {};      // dynamic shared memory of the class's kernel
+    int thread_max_h = 0;              // largest |N_H(v)| of the thread items
 };
 
 struct tc_graph {
